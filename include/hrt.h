@@ -1,0 +1,236 @@
+/*
+ * hrt.h - C ABI of the GB300 Monte-Carlo dust continuum radiative transfer library (libhrt).
+ *
+ * The library computes the iterative LTE dust temperature of Robitaille (2011), HYPERION,
+ * Sects. 2.2-2.6: photon packets are emitted from point and cell sources, propagated
+ * through a Cartesian or spherical-polar grid of constant-density cells to a sampled
+ * optical depth, scattered (Henyey-Greenstein) or absorbed and re-emitted, and the path
+ * lengths they travel give the absorbed energy rate of every cell (Eq. 2); the cell
+ * temperatures follow from the Planck-mean balance (Eq. 3), the iteration is repeated
+ * until the percentile test of Sect. 2.4 (Eqs. 4-6) passes, and SEDs and images are
+ * formed by peeling-off (Sect. 2.6.2).
+ *
+ * Conventions (all entry points)
+ *   - Every function returns 0 (HRT_OK) or a negative hrt_status; hrt_last_error() holds a
+ *     one-line message for the last failure on that context.
+ *   - Units are cgs: lengths cm, angles rad, frequencies Hz, luminosities erg/s, densities
+ *     g/cm^3, opacities cm^2/g, temperatures K.  The emission time step is dt = 1 s.
+ *   - Cell arrays are C-ordered [n3][n2][n1]: Cartesian [z][y][x], spherical [phi][theta][r].
+ *   - Host input arrays are copied; the caller keeps ownership and may free them on return.
+ *     Host output arrays are caller-owned and must hold at least the stated count n
+ *     (HRT_EINVAL otherwise).  *_device variants take device pointers and are ordered on the
+ *     context's stream.
+ *   - All device memory the context needs is allocated and owned by the context and freed by
+ *     hrt_destroy().  `stream` arguments are cudaStream_t values passed as void*.
+ *   - The context is not thread-safe; use one context per host thread.
+ */
+#ifndef HRT_H
+#define HRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HRT_OK = 0,
+    HRT_EINVAL = -1,     /* bad argument (size, NaN, ordering, range) */
+    HRT_ENOMEM = -2,     /* device or host allocation failed */
+    HRT_ESTATE = -3,     /* call order: e.g. run before grid/density/dust/sources are set */
+    HRT_ECUDA = -4,      /* a CUDA runtime call failed (message holds cudaGetErrorString) */
+    HRT_ETIMEDOUT = -5,  /* the propagation watchdog expired; results of the call are partial */
+    HRT_ERANGE = -6      /* a value beyond a table (strict mode) */
+} hrt_status;
+
+typedef struct hrt_ctx hrt_ctx;
+typedef struct hrt_batch hrt_batch;
+
+/* ------------------------------------------------------------------ lifetime */
+
+/* Create a context on CUDA device `device`.  `seed` keys the Philox4x32-10 streams of all
+ * packets (Salmon et al. 2011): packet p of iteration i draws from counters
+ * (draw block, p, i, model id) under key (seed low 32 bits, seed high 32 bits).
+ * `stream` (cudaStream_t, may be NULL = legacy default stream) orders all device work. */
+int hrt_create(hrt_ctx** out, int device, uint64_t seed, void* stream);
+int hrt_destroy(hrt_ctx* ctx);
+const char* hrt_last_error(const hrt_ctx* ctx);
+int hrt_set_stream(hrt_ctx* ctx, void* stream);
+/* Library version string, e.g. "hrt 0.1 sm_103a". */
+const char* hrt_version(void);
+
+/* ------------------------------------------------------------------ problem (Sect. 2.1) */
+
+/* Cartesian grid (Sect. 2.1.2): nx+1, ny+1, nz+1 strictly increasing wall coordinates (cm).
+ * Resetting the grid discards density, temperatures and cell sources. */
+int hrt_set_grid_cartesian(hrt_ctx* ctx, int nx, int ny, int nz,
+                           const double* xw, const double* yw, const double* zw);
+
+/* Spherical-polar grid (Sect. 2.1.2): radii rw[0..nr] (rw[0] >= 0; rw[0] > 0 leaves an empty
+ * inner hole that packets cross without interacting), polar walls tw[0..nt] with tw[0] = 0 and
+ * tw[nt] = pi, azimuthal walls pw[0..np] with pw[0] = 0, pw[np] = 2 pi and every cell at most
+ * pi wide.  All strictly increasing. */
+int hrt_set_grid_spherical(hrt_ctx* ctx, int nr, int nt, int np,
+                           const double* rw, const double* tw, const double* pw);
+
+/* Dust density per cell (g/cm^3), n = number of cells, finite and >= 0.  Cells of zero density
+ * hold no dust: packets cross them without interacting or depositing. */
+int hrt_set_density(hrt_ctx* ctx, const float* rho, int64_t n);
+
+/* One dust type (Sect. 2.1.3): nnu strictly increasing frequencies nu (Hz) with mass
+ * extinction chi (cm^2/g, > 0) and albedo in [0,1]; Henyey-Greenstein asymmetry g in (-1,1).
+ * Between nodes chi is interpolated log-log and the albedo linearly in log nu.  nT strictly
+ * increasing temperature nodes (K) span the emissivity table: the library tabulates
+ * E(T) = 4 pi int kappa_nu B_nu(T) dnu (Eq. 3, kappa = (1 - albedo) chi, trapezoid rule over
+ * the nodes) and the cumulative emissivity kappa_nu B_nu(T) of each node for re-emission. */
+int hrt_set_dust(hrt_ctx* ctx, int nnu, const double* nu, const double* chi, const double* albedo,
+                 double g, int nT, const double* T);
+
+/* Isotropic point source (Sect. 2.1.1) at x[3] (cm, inside the grid or its inner hole) with
+ * luminosity L (erg/s) and a blackbody spectrum of temperature Teff, tabulated on 1000
+ * log-spaced frequencies over the dust band and renormalised to carry all of L. */
+int hrt_add_point_source(hrt_ctx* ctx, const double x[3], double L, double Teff);
+
+/* Point source with a user spectrum f_nu on n strictly increasing frequencies (any positive
+ * normalisation; the part inside the dust band carries all of L). */
+int hrt_add_point_source_spectrum(hrt_ctx* ctx, const double x[3], double L, int n,
+                                  const double* nu, const double* fnu);
+
+/* Diffuse source (Sect. 2.1.1): luminosity per cell Lcell[n] (erg/s, >= 0) emitted from a
+ * position uniform in the cell volume with an isotropic direction and a blackbody spectrum of
+ * temperature Teff.  Replaces any previous cell source. */
+int hrt_set_cell_source(hrt_ctx* ctx, const double* Lcell, int64_t n, double Teff);
+int hrt_clear_sources(hrt_ctx* ctx);
+
+/* Observers for peeling-off (Sect. 2.6.2): nobs directions given by inclination incl[o] and
+ * azimuth az[o] (rad), observer unit vector n = (sin i cos az, sin i sin az, cos i).  SEDs have
+ * nsed log-spaced wavelength bins over [lam_min_um, lam_max_um] (microns) and hold
+ * erg/s/sr per bin.  Images (img_nx > 0) are img_nx x img_ny pixels over +-img_half_extent_cm
+ * on the sky plane (axes e_x = (-sin az, cos az, 0), e_y = n x e_x) at the nimg wavelengths
+ * img_lam_um, each collecting the packets of the SED bin holding that wavelength. */
+int hrt_set_peeloff(hrt_ctx* ctx, int nobs, const double* incl, const double* az, int nsed,
+                    double lam_min_um, double lam_max_um, int img_nx, int img_ny,
+                    double img_half_extent_cm, int nimg, const double* img_lam_um);
+
+/* ------------------------------------------------------------------ iteration (Sects. 2.2-2.4) */
+
+typedef enum { HRT_KERNEL_EVENT = 0, HRT_KERNEL_PLAIN = 1 } hrt_kernel;
+
+typedef struct {
+    int64_t max_interactions;    /* per packet; a packet beyond it is killed and its energy tallied */
+    int32_t peel;                /* 1: peel-off into the SED/image bins (zeroed at the start of the call) */
+    int32_t update_temperature;  /* 1: Lucy iteration (Eqs. 2-6); 0: imaging pass, temperatures kept */
+    int32_t terminate_on_absorb; /* test mode: an absorbed packet ends instead of being re-emitted */
+    int32_t quantity;            /* convergence quantity: 0 temperature, 1 Adot (the paper's choice) */
+    double p;                    /* percentile of Sect. 2.4 (e.g. 0.99) */
+    double q_thres;              /* Q threshold (e.g. 1.02 on T, 2 on Adot) */
+    double delta_thres;          /* Delta threshold (INFINITY disables the Delta test) */
+    int32_t kernel;              /* hrt_kernel */
+    int32_t block_size;          /* threads per block, 0 = tuned default */
+    int32_t blocks_per_sm;       /* persistent blocks per SM, 0 = tuned default */
+    int32_t regroup_threshold;   /* event kernel: a warp leaves the walk phase when fewer lanes
+                                    than this are still walking (1..32, 0 = tuned default) */
+    double watchdog_ms;          /* > 0: the propagation kernel stops after this long and the call
+                                    returns HRT_ETIMEDOUT (the context stays usable) */
+} hrt_run_params;
+
+typedef struct {
+    int32_t iteration;           /* index of the iteration that ran (0-based) */
+    int32_t converged;           /* Q < q_thres and Delta < delta_thres */
+    double Q;                    /* Eq. 5-6: p-quantile of delta(prev, new) over cells with dust */
+    double Delta;                /* Eq. 6: delta(Q_prev, Q); INFINITY on the first iteration */
+    double e_emitted, e_escaped, e_killed, e_absorbed;   /* erg over dt = 1 s */
+    int64_t n_packets, n_interactions, n_scatter, n_absorb;
+    int64_t n_crossings;         /* propagation cell crossings */
+    int64_t n_peel_crossings;    /* peel-off ray cell crossings */
+    int64_t n_killed;
+    int64_t clamp_low, clamp_high;   /* cells (with dust) whose Adot fell outside E(T) */
+    double ms_propagate;         /* device time of the propagation kernel */
+    double ms_total;             /* device time of the whole call */
+    int64_t kernel_launches;     /* kernels the call launched */
+} hrt_iter_stats;
+
+/* Defaults: max_interactions 1e6, peel 0, update_temperature 1, p 0.99, q_thres 1.02 on T,
+ * delta_thres INFINITY, event kernel, tuned launch shape, no watchdog. */
+void hrt_default_params(hrt_run_params* p);
+
+/* Run one iteration with n_packets packets of energy eps = L_total dt / n_packets.  In a Lucy
+ * iteration the absorbed-energy accumulators are zeroed, packets propagate with the
+ * temperatures of the previous iteration (10 K before the first), then Adot = acc/(V dt)
+ * (Eq. 2) and T from Eq. 3 (table clamps counted) replace the previous values and Q, Delta
+ * are formed (Eqs. 4-6).  Blocks until the statistics are on the host.  `out` may be NULL. */
+int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* params, hrt_iter_stats* out);
+
+/* ------------------------------------------------------------------ read-out / state */
+
+int hrt_get_temperature(hrt_ctx* ctx, double* out, int64_t n);        /* K, [cells] */
+int hrt_get_specific_energy(hrt_ctx* ctx, double* out, int64_t n);    /* Adot, erg/s/g, [cells] */
+int hrt_get_absorbed(hrt_ctx* ctx, double* out, int64_t n);           /* raw sum eps kappa l, [cells] */
+int hrt_get_sed(hrt_ctx* ctx, double* out, int64_t n);                /* [nobs][nsed] erg/s/sr */
+int hrt_get_image(hrt_ctx* ctx, double* out, int64_t n);              /* [nobs][nimg][ny][nx] */
+int hrt_get_escape(hrt_ctx* ctx, double* out, int64_t n);             /* [10 cos(theta) bins][nsed] erg/s */
+int hrt_get_temperature_device(hrt_ctx* ctx, double* d_out, int64_t n);
+int hrt_get_sed_device(hrt_ctx* ctx, double* d_out, int64_t n);
+int64_t hrt_num_cells(const hrt_ctx* ctx);
+
+/* Warm start / resume: replace the temperatures (K, > 0) used by the next iteration. */
+int hrt_set_temperature(hrt_ctx* ctx, const double* T, int64_t n);
+int hrt_set_temperature_device(hrt_ctx* ctx, const double* d_T, int64_t n);
+/* Set the iteration counter (it keys the random streams, so a resumed run repeats them). */
+int hrt_set_iteration(hrt_ctx* ctx, int iteration);
+int hrt_set_model_id(hrt_ctx* ctx, uint32_t model_id);
+
+/* ------------------------------------------------------------------ single steps (test hooks)
+ * Each runs one step of the method on n independent inputs in device memory with given
+ * uniform deviates, so that it can be compared element by element with a CPU reference. */
+
+/* Philox4x32-10: out[4i..4i+3] = philox(ctr[4i..4i+3], key[2i..2i+1]). */
+int hrt_step_philox(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, void* stream);
+
+/* Cell exit along the context grid (Sect. 2.2): pos/dir [n][3] (cm, unit), cell [n][3]
+ * (per-axis indices); writes the distance to the exit (cm) and axis*2 + (sense > 0). */
+int hrt_step_cell_exit(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir,
+                       const int32_t* d_cell, float* d_dist, int32_t* d_exit);
+
+/* Extinction optical depth from pos along dir to the grid boundary at frequency nu[n]
+ * (the peel-off ray of Sect. 2.6.2). */
+int hrt_step_tau_to_edge(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir,
+                         const float* d_nu, float* d_tau);
+
+/* Henyey-Greenstein scattering: new direction from dir_in [n][3] and uniforms u1 (cos theta)
+ * and u2 (azimuth). */
+int hrt_step_hg_scatter(hrt_ctx* ctx, int64_t n, const float* d_dir_in, const float* d_u1,
+                        const float* d_u2, float* d_dir_out);
+
+/* Re-emission frequency from emissivity row[n] (temperature node) with uniform u[n]. */
+int hrt_step_sample_emission(hrt_ctx* ctx, int64_t n, const int32_t* d_row, const float* d_u, float* d_nu);
+
+/* Source spectrum frequency of source src[n] with uniform u[n]. */
+int hrt_step_sample_source(hrt_ctx* ctx, int64_t n, const int32_t* d_src, const float* d_u, float* d_nu);
+
+/* Temperature from Adot (Eq. 3 inversion on the library's table). */
+int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* d_T);
+
+/* Tabulated E(T) [nT] and emissivity cdf [nT][nnu] as built on the device (copied to host). */
+int hrt_get_tables(hrt_ctx* ctx, double* E, int64_t nE, float* cdf, int64_t ncdf);
+
+/* ------------------------------------------------------------------ batched models (Sect. 3 analogue)
+ * Many contexts on the same device run each Lucy iteration in one persistent launch whose
+ * blocks pull (model, packet chunk) work items from a device queue (largest first), the
+ * device-side form of the paper's dynamic chunk scheduling.  Each model keeps its own
+ * seed, tables and convergence state; a converged model drops out of later iterations. */
+int hrt_batch_create(hrt_batch** out, hrt_ctx* const* models, int n);
+int hrt_batch_destroy(hrt_batch* b);
+/* Run up to max_iter Lucy iterations for every unconverged model, n_packets[m] packets each,
+ * one persistent launch per iteration (captured as a CUDA graph after the first).  Writes the
+ * last stats of every model to per_model_out[n] (may be NULL) and the number of iterations run
+ * to *iterations_run (may be NULL). */
+int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hrt_run_params* params,
+                  hrt_iter_stats* per_model_out, int* iterations_run);
+/* Time a few launch shapes on one iteration's worth of work and keep the fastest. */
+int hrt_batch_tune(hrt_batch* b, const int64_t* n_packets);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HRT_H */

@@ -1,0 +1,999 @@
+// Host runtime of libhrt: the C ABI of include/hrt.h.  Owns the device memory of a context,
+// validates and stages the problem description, builds the device tables and drives one Lucy
+// iteration as a stream-ordered sequence of kernels with a single statistics copy at the end.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hrt.h"
+#include "hrt_internal.h"
+
+using namespace hrt;
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double C_LIGHT_CGS = 2.99792458e10;
+constexpr int NSPEC = 1000;            // source spectrum nodes over the dust band
+constexpr int DEFAULT_NSED = 250;
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count) {
+        if (count == n && p) return cudaSuccess;
+        release();
+        if (count == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        n = count;
+        return cudaSuccess;
+    }
+    cudaError_t upload(const T* h, size_t count, cudaStream_t s) {
+        cudaError_t e = alloc(count);
+        if (e != cudaSuccess || count == 0) return e;
+        return cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct PointSrc {
+    double x[3];
+    double L;
+    double teff;
+    std::vector<double> unu, uf;
+};
+
+}  // namespace
+
+struct hrt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t seed = 0;
+    uint32_t model_id = 0;
+    int iteration = 0;
+    std::string err;
+
+    // ---- problem (host copies)
+    int gtype = -1;
+    int n[3] = {0, 0, 0};
+    std::vector<double> w[3];
+    double L0 = 1.0;
+    std::vector<float> rho;
+    int64_t n_dust = 0;
+    std::vector<double> nu, chi, alb, Tn;
+    double g = 0.0;
+    std::vector<PointSrc> pts;
+    std::vector<double> Lcell;
+    double cell_teff = 0.0;
+    int nobs = 0, nsed = DEFAULT_NSED, img_nx = 0, img_ny = 0, nimg = 0;
+    double lam_min_um = 0.1, lam_max_um = 1000.0, img_half = 0.0;
+    std::vector<double> incl, az, img_lam;
+    bool dirty_grid = true, dirty_dust = true, dirty_src = true, dirty_obs = true, have_T = false;
+
+    // ---- device problem
+    DBuf<float> d_rhoL, d_w1, d_w2, d_w3, d_rw, d_r2w, d_thw, d_cth, d_sth, d_phw, d_cph, d_sph;
+    DBuf<double> d_rwd, d_cthd, d_sthd, d_va, d_vb, d_vc;
+    DBuf<float> d_lnu, d_inv_dlnu, d_lchi, d_alb, d_nuf, d_cdf_emit;
+    DBuf<double> d_nu, d_kappa, d_Tn, d_lnT, d_E, d_lnE;
+    DBuf<float> d_src_pos, d_spec_nu, d_spec_cdf;
+    DBuf<double> d_src_cdf, d_cell_cdf, d_spec_nud, d_teff, d_unu, d_uf;
+    DBuf<int> d_uoff, d_un;
+    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey;
+    DBuf<int32_t> d_img_bin;
+    // ---- device state
+    DBuf<double> d_T, d_adot, d_acc, d_sed, d_img;
+    DBuf<int32_t> d_row;
+    DBuf<unsigned long long> d_keys, d_esc, d_counters, d_state;
+    DBuf<unsigned int> d_hist;
+    DBuf<int32_t> d_abort;
+    DBuf<unsigned long long> d_work;
+    unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    double Q_prev = std::numeric_limits<double>::infinity();
+    bool have_Q = false;
+    double L_tot = 0.0;
+    double last_eps = 0.0;
+
+    DevGrid grid{};
+    DevDust dust{};
+    DevSources src{};
+    DevObs obs{};
+
+    int fail(int code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return HRT_OK;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? HRT_ENOMEM : HRT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    int64_t ncells() const { return (int64_t)n[0] * n[1] * n[2]; }
+};
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        int _rc = ctx->cuda((call), what);               \
+        if (_rc != HRT_OK) return _rc;                   \
+    } while (0)
+
+namespace {
+
+bool finite_all(const double* a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+bool increasing(const double* a, int64_t n) {
+    for (int64_t i = 1; i < n; ++i)
+        if (!(a[i] > a[i - 1])) return false;
+    return true;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- staging
+int stage_grid(hrt_ctx* ctx) {
+    const cudaStream_t s = ctx->stream;
+    const int64_t nc = ctx->ncells();
+    std::vector<float> rhoL(nc);
+    for (int64_t c = 0; c < nc; ++c) rhoL[c] = (float)((double)ctx->rho[c] * ctx->L0);
+    CK(ctx->d_rhoL.upload(rhoL.data(), nc, s), "upload density");
+    DevGrid& g = ctx->grid;
+    g = DevGrid{};
+    g.type = ctx->gtype;
+    g.n1 = ctx->n[0]; g.n2 = ctx->n[1]; g.n3 = ctx->n[2];
+    g.ncells = nc;
+    std::vector<double> va(ctx->n[0]), vb(ctx->n[1]), vc(ctx->n[2]);
+    if (ctx->gtype == GRID_CARTESIAN) {
+        std::vector<float> ws[3];
+        for (int a = 0; a < 3; ++a) {
+            ws[a].resize(ctx->w[a].size());
+            for (size_t i = 0; i < ws[a].size(); ++i) ws[a][i] = (float)(ctx->w[a][i] / ctx->L0);
+        }
+        CK(ctx->d_w1.upload(ws[0].data(), ws[0].size(), s), "upload walls");
+        CK(ctx->d_w2.upload(ws[1].data(), ws[1].size(), s), "upload walls");
+        CK(ctx->d_w3.upload(ws[2].data(), ws[2].size(), s), "upload walls");
+        g.w1 = ctx->d_w1.p; g.w2 = ctx->d_w2.p; g.w3 = ctx->d_w3.p;
+        for (int i = 0; i < ctx->n[0]; ++i) va[i] = ctx->w[0][i + 1] - ctx->w[0][i];
+        for (int j = 0; j < ctx->n[1]; ++j) vb[j] = ctx->w[1][j + 1] - ctx->w[1][j];
+        for (int k = 0; k < ctx->n[2]; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
+    } else {
+        const int nr = ctx->n[0], nt = ctx->n[1], np = ctx->n[2];
+        std::vector<float> rw(nr + 1), r2w(nr + 1), thw(nt + 1), cth(nt + 1), sth(nt + 1), phw(np + 1), cph(np + 1),
+            sph(np + 1);
+        std::vector<double> rwd(nr + 1), cthd(nt + 1), sthd(nt + 1);
+        for (int i = 0; i <= nr; ++i) {
+            rwd[i] = ctx->w[0][i] / ctx->L0;
+            rw[i] = (float)rwd[i];
+            r2w[i] = (float)(rwd[i] * rwd[i]);
+        }
+        for (int j = 0; j <= nt; ++j) {
+            const double t = ctx->w[1][j];
+            double c = std::cos(t), sn = std::sin(t);
+            if (std::fabs(c) < 1e-12) c = 0.0;      // the midplane wall is the plane z = 0
+            thw[j] = (float)t;
+            cthd[j] = c; sthd[j] = sn;
+            cth[j] = (float)c; sth[j] = (float)sn;
+        }
+        for (int k = 0; k <= np; ++k) {
+            const double p = ctx->w[2][k];
+            phw[k] = (float)p;
+            cph[k] = (float)std::cos(p);
+            sph[k] = (float)std::sin(p);
+        }
+        CK(ctx->d_rw.upload(rw.data(), rw.size(), s), "walls");
+        CK(ctx->d_r2w.upload(r2w.data(), r2w.size(), s), "walls");
+        CK(ctx->d_rwd.upload(rwd.data(), rwd.size(), s), "walls");
+        CK(ctx->d_thw.upload(thw.data(), thw.size(), s), "walls");
+        CK(ctx->d_cth.upload(cth.data(), cth.size(), s), "walls");
+        CK(ctx->d_sth.upload(sth.data(), sth.size(), s), "walls");
+        CK(ctx->d_cthd.upload(cthd.data(), cthd.size(), s), "walls");
+        CK(ctx->d_sthd.upload(sthd.data(), sthd.size(), s), "walls");
+        CK(ctx->d_phw.upload(phw.data(), phw.size(), s), "walls");
+        CK(ctx->d_cph.upload(cph.data(), cph.size(), s), "walls");
+        CK(ctx->d_sph.upload(sph.data(), sph.size(), s), "walls");
+        g.rw = ctx->d_rw.p; g.r2w = ctx->d_r2w.p; g.rwd = ctx->d_rwd.p;
+        g.thw = ctx->d_thw.p; g.cth = ctx->d_cth.p; g.sth = ctx->d_sth.p; g.cthd = ctx->d_cthd.p; g.sthd = ctx->d_sthd.p;
+        g.phw = ctx->d_phw.p; g.cph = ctx->d_cph.p; g.sph = ctx->d_sph.p;
+        g.r0 = rw[0];
+        // FP64 sphere solves within four inner radii (or the first shell without a hole)
+        g.r_fp64 = (float)(4.0 * (rwd[0] > 0 ? rwd[0] : rwd[1]));
+        g.sin_fp64 = 0.1f;
+        for (int i = 0; i < nr; ++i) va[i] = (std::pow(ctx->w[0][i + 1], 3) - std::pow(ctx->w[0][i], 3)) / 3.0;
+        for (int j = 0; j < nt; ++j) vb[j] = std::cos(ctx->w[1][j]) - std::cos(ctx->w[1][j + 1]);
+        for (int k = 0; k < np; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
+    }
+    CK(ctx->d_va.upload(va.data(), va.size(), s), "volumes");
+    CK(ctx->d_vb.upload(vb.data(), vb.size(), s), "volumes");
+    CK(ctx->d_vc.upload(vc.data(), vc.size(), s), "volumes");
+    g.rhoL = ctx->d_rhoL.p;
+    // per-cell state
+    CK(ctx->d_acc.alloc(nc), "alloc acc");
+    CK(ctx->d_adot.alloc(nc), "alloc adot");
+    CK(ctx->d_row.alloc(nc), "alloc rows");
+    CK(ctx->d_keys.alloc(nc), "alloc keys");
+    if (!ctx->have_T || ctx->d_T.n != (size_t)nc) {
+        std::vector<double> T0(nc, 10.0);   // cold start
+        CK(ctx->d_T.upload(T0.data(), nc, s), "upload T");
+        CK(cudaMemsetAsync(ctx->d_adot.p, 0, nc * sizeof(double), s), "zero adot");
+        ctx->have_T = true;
+    }
+    ctx->dirty_grid = false;
+    return HRT_OK;
+}
+
+int stage_dust(hrt_ctx* ctx) {
+    const cudaStream_t s = ctx->stream;
+    const int nnu = (int)ctx->nu.size(), nT = (int)ctx->Tn.size();
+    std::vector<float> lnu(nnu), inv(nnu), lchi(nnu), alb(nnu), nuf(nnu);
+    std::vector<double> kappa(nnu), lnT(nT);
+    for (int k = 0; k < nnu; ++k) {
+        lnu[k] = (float)std::log(ctx->nu[k]);
+        lchi[k] = (float)std::log(ctx->chi[k]);
+        alb[k] = (float)ctx->alb[k];
+        nuf[k] = (float)ctx->nu[k];
+        kappa[k] = (1.0 - ctx->alb[k]) * ctx->chi[k];
+        inv[k] = k + 1 < nnu ? (float)(1.0 / (std::log(ctx->nu[k + 1]) - std::log(ctx->nu[k]))) : 0.f;
+    }
+    for (int m = 0; m < nT; ++m) lnT[m] = std::log(ctx->Tn[m]);
+    CK(ctx->d_lnu.upload(lnu.data(), nnu, s), "dust");
+    CK(ctx->d_inv_dlnu.upload(inv.data(), nnu, s), "dust");
+    CK(ctx->d_lchi.upload(lchi.data(), nnu, s), "dust");
+    CK(ctx->d_alb.upload(alb.data(), nnu, s), "dust");
+    CK(ctx->d_nuf.upload(nuf.data(), nnu, s), "dust");
+    CK(ctx->d_nu.upload(ctx->nu.data(), nnu, s), "dust");
+    CK(ctx->d_kappa.upload(kappa.data(), nnu, s), "dust");
+    CK(ctx->d_Tn.upload(ctx->Tn.data(), nT, s), "dust");
+    CK(ctx->d_lnT.upload(lnT.data(), nT, s), "dust");
+    CK(ctx->d_E.alloc(nT), "tables");
+    CK(ctx->d_lnE.alloc(nT), "tables");
+    CK(ctx->d_cdf_emit.alloc((size_t)nT * nnu), "tables");
+    CK(launch_emission_tables(nnu, ctx->d_nu.p, ctx->d_kappa.p, nT, ctx->d_Tn.p, ctx->d_E.p, ctx->d_lnE.p,
+                              ctx->d_cdf_emit.p, s),
+       "emission tables");
+    DevDust& d = ctx->dust;
+    d.nnu = nnu; d.nT = nT;
+    d.lnu = ctx->d_lnu.p; d.inv_dlnu = ctx->d_inv_dlnu.p; d.lchi = ctx->d_lchi.p; d.alb = ctx->d_alb.p;
+    d.nu = ctx->d_nuf.p; d.cdf_emit = ctx->d_cdf_emit.p; d.g = (float)ctx->g;
+    ctx->dirty_dust = false;
+    ctx->dirty_src = true;   // source spectra span the dust band
+    return HRT_OK;
+}
+
+int stage_sources(hrt_ctx* ctx) {
+    const cudaStream_t s = ctx->stream;
+    const int npt = (int)ctx->pts.size();
+    const bool cell = !ctx->Lcell.empty();
+    const int nsrc = npt + (cell ? 1 : 0);
+    std::vector<double> L(nsrc), teff(nsrc), unu, uf;
+    std::vector<int> uoff(nsrc, 0), un(nsrc, 0);
+    std::vector<float> pos(3 * std::max(npt, 1), 0.f);
+    for (int i = 0; i < npt; ++i) {
+        L[i] = ctx->pts[i].L;
+        teff[i] = ctx->pts[i].teff;
+        for (int a = 0; a < 3; ++a) pos[3 * i + a] = (float)(ctx->pts[i].x[a] / ctx->L0);
+        uoff[i] = (int)unu.size();
+        un[i] = (int)ctx->pts[i].unu.size();
+        unu.insert(unu.end(), ctx->pts[i].unu.begin(), ctx->pts[i].unu.end());
+        uf.insert(uf.end(), ctx->pts[i].uf.begin(), ctx->pts[i].uf.end());
+    }
+    if (cell) {
+        double tot = 0.0;
+        std::vector<double> cc(ctx->Lcell.size());
+        for (size_t c = 0; c < cc.size(); ++c) { tot += ctx->Lcell[c]; cc[c] = tot; }
+        for (auto& v : cc) v /= tot;
+        cc.back() = 1.0;
+        CK(ctx->d_cell_cdf.upload(cc.data(), cc.size(), s), "cell source");
+        L[npt] = tot;
+        teff[npt] = ctx->cell_teff;
+    }
+    double cum = 0.0;
+    std::vector<double> cdf(nsrc);
+    for (int i = 0; i < nsrc; ++i) { cum += L[i]; cdf[i] = cum; }
+    ctx->L_tot = cum;
+    for (auto& v : cdf) v /= cum;
+    cdf.back() = 1.0;
+    // spectrum grid: NSPEC log-spaced frequencies over the dust band
+    std::vector<double> snu(NSPEC);
+    const double a = ctx->nu.front(), b = ctx->nu.back();
+    for (int k = 0; k < NSPEC; ++k) snu[k] = a * std::pow(b / a, (double)k / (NSPEC - 1));
+    snu.front() = a;
+    snu.back() = b;
+    std::vector<float> snuf(snu.begin(), snu.end());
+    if (unu.empty()) { unu.push_back(0.0); uf.push_back(0.0); }
+    CK(ctx->d_src_pos.upload(pos.data(), pos.size(), s), "sources");
+    CK(ctx->d_src_cdf.upload(cdf.data(), nsrc, s), "sources");
+    CK(ctx->d_spec_nud.upload(snu.data(), NSPEC, s), "sources");
+    CK(ctx->d_spec_nu.upload(snuf.data(), NSPEC, s), "sources");
+    CK(ctx->d_teff.upload(teff.data(), nsrc, s), "sources");
+    CK(ctx->d_unu.upload(unu.data(), unu.size(), s), "sources");
+    CK(ctx->d_uf.upload(uf.data(), uf.size(), s), "sources");
+    CK(ctx->d_uoff.upload(uoff.data(), nsrc, s), "sources");
+    CK(ctx->d_un.upload(un.data(), nsrc, s), "sources");
+    CK(ctx->d_spec_cdf.alloc((size_t)nsrc * NSPEC), "sources");
+    CK(launch_source_spectra(nsrc, NSPEC, ctx->d_spec_nud.p, ctx->d_teff.p, ctx->d_unu.p, ctx->d_uf.p, ctx->d_uoff.p,
+                             ctx->d_un.p, ctx->d_spec_cdf.p, s),
+       "source spectra");
+    DevSources& S = ctx->src;
+    S.npoint = npt; S.nsrc = nsrc; S.nspec = NSPEC;
+    S.pos = ctx->d_src_pos.p; S.cdf = ctx->d_src_cdf.p; S.spec_nu = ctx->d_spec_nu.p; S.spec_cdf = ctx->d_spec_cdf.p;
+    S.cell_cdf = cell ? ctx->d_cell_cdf.p : nullptr;
+    ctx->dirty_src = false;
+    return HRT_OK;
+}
+
+int stage_observers(hrt_ctx* ctx) {
+    const cudaStream_t s = ctx->stream;
+    const int no = ctx->nobs;
+    std::vector<float> n(3 * std::max(no, 1)), ex(3 * std::max(no, 1)), ey(3 * std::max(no, 1));
+    for (int o = 0; o < no; ++o) {
+        const double i = ctx->incl[o], p = ctx->az[o];
+        const double nn[3] = {std::sin(i) * std::cos(p), std::sin(i) * std::sin(p), std::cos(i)};
+        const double e1[3] = {-std::sin(p), std::cos(p), 0.0};
+        const double e2[3] = {nn[1] * e1[2] - nn[2] * e1[1], nn[2] * e1[0] - nn[0] * e1[2], nn[0] * e1[1] - nn[1] * e1[0]};
+        for (int a = 0; a < 3; ++a) { n[3 * o + a] = (float)nn[a]; ex[3 * o + a] = (float)e1[a]; ey[3 * o + a] = (float)e2[a]; }
+    }
+    const double lmin = ctx->lam_min_um * 1e-4, lmax = ctx->lam_max_um * 1e-4;
+    std::vector<int32_t> ib(std::max(ctx->nimg, 1), -1);
+    for (int l = 0; l < ctx->nimg; ++l) {
+        const double lam = ctx->img_lam[l] * 1e-4;
+        const double x = ctx->nsed * std::log(lam / lmin) / std::log(lmax / lmin);
+        ib[l] = (x >= 0 && x < ctx->nsed) ? (int)std::floor(x) : -1;
+    }
+    CK(ctx->d_obs_n.upload(n.data(), n.size(), s), "observers");
+    CK(ctx->d_obs_ex.upload(ex.data(), ex.size(), s), "observers");
+    CK(ctx->d_obs_ey.upload(ey.data(), ey.size(), s), "observers");
+    CK(ctx->d_img_bin.upload(ib.data(), ib.size(), s), "observers");
+    DevObs& O = ctx->obs;
+    O.nobs = no; O.nsed = ctx->nsed;
+    O.img_nx = ctx->img_nx; O.img_ny = ctx->img_ny; O.nimg = ctx->img_nx > 0 ? ctx->nimg : 0;
+    O.n = ctx->d_obs_n.p; O.ex = ctx->d_obs_ex.p; O.ey = ctx->d_obs_ey.p;
+    // bin = floor(nsed ln(lambda/lmin)/ln(lmax/lmin)), lambda = c/nu
+    const double den = std::log(lmax / lmin);
+    O.sed_b = ctx->nsed / den;
+    O.sed_a = ctx->nsed * (std::log(C_LIGHT_CGS) - std::log(lmin)) / den;
+    O.img_half = (float)(ctx->img_half / ctx->L0);
+    O.img_scale = ctx->img_half > 0 ? (float)(ctx->img_nx / (2.0 * ctx->img_half / ctx->L0)) : 0.f;
+    O.img_bin = ctx->d_img_bin.p;
+    CK(ctx->d_sed.alloc(std::max<size_t>(1, (size_t)no * ctx->nsed)), "sed");
+    CK(ctx->d_img.alloc(std::max<size_t>(1, (size_t)no * O.nimg * ctx->img_nx * ctx->img_ny)), "image");
+    CK(ctx->d_esc.alloc((size_t)N_ESC_MU * ctx->nsed), "escape");
+    ctx->dirty_obs = false;
+    return HRT_OK;
+}
+
+int prepare(hrt_ctx* ctx) {
+    if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "grid not set");
+    if ((int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "density not set");
+    if (ctx->nu.empty()) return ctx->fail(HRT_ESTATE, "dust not set");
+    if (ctx->pts.empty() && ctx->Lcell.empty()) return ctx->fail(HRT_ESTATE, "no sources");
+    int rc;
+    if (ctx->dirty_grid && (rc = stage_grid(ctx)) != HRT_OK) return rc;
+    if (ctx->dirty_dust && (rc = stage_dust(ctx)) != HRT_OK) return rc;
+    if (ctx->dirty_src && (rc = stage_sources(ctx)) != HRT_OK) return rc;
+    if (ctx->dirty_obs && (rc = stage_observers(ctx)) != HRT_OK) return rc;
+    ctx->dust.emit_row = ctx->d_row.p;
+    CK(ctx->d_counters.alloc(N_COUNTERS + 4), "counters");
+    CK(ctx->d_state.alloc(4), "select state");
+    CK(ctx->d_hist.alloc(256), "select histogram");
+    CK(ctx->d_abort.alloc(1), "abort flag");
+    CK(ctx->d_work.alloc(2), "work counter");
+    if (!ctx->h_stats) CK(cudaMallocHost(&ctx->h_stats, sizeof(unsigned long long) * (N_COUNTERS + 8)), "pinned stats");
+    for (auto& e : ctx->ev)
+        if (!e) CK(cudaEventCreate(&e), "event");
+    return HRT_OK;
+}
+
+}  // namespace
+
+// ==================================================================== ABI
+extern "C" {
+
+const char* hrt_version(void) { return "hrt 0.1 sm_103a"; }
+
+int hrt_create(hrt_ctx** out, int device, uint64_t seed, void* stream) {
+    if (!out) return HRT_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HRT_ECUDA;
+    }
+    hrt_ctx* ctx = new (std::nothrow) hrt_ctx();
+    if (!ctx) return HRT_ENOMEM;
+    ctx->device = device;
+    ctx->seed = seed;
+    ctx->stream = (cudaStream_t)stream;
+    *out = ctx;
+    return HRT_OK;
+}
+
+int hrt_destroy(hrt_ctx* ctx) {
+    if (!ctx) return HRT_EINVAL;
+    DeviceGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto* b : {&ctx->d_rhoL, &ctx->d_w1, &ctx->d_w2, &ctx->d_w3, &ctx->d_rw, &ctx->d_r2w, &ctx->d_thw, &ctx->d_cth,
+                    &ctx->d_sth, &ctx->d_phw, &ctx->d_cph, &ctx->d_sph, &ctx->d_lnu, &ctx->d_inv_dlnu, &ctx->d_lchi,
+                    &ctx->d_alb, &ctx->d_nuf, &ctx->d_cdf_emit, &ctx->d_src_pos, &ctx->d_spec_nu, &ctx->d_spec_cdf,
+                    &ctx->d_obs_n, &ctx->d_obs_ex, &ctx->d_obs_ey})
+        b->release();
+    for (auto* b : {&ctx->d_rwd, &ctx->d_cthd, &ctx->d_sthd, &ctx->d_va, &ctx->d_vb, &ctx->d_vc, &ctx->d_nu,
+                    &ctx->d_kappa, &ctx->d_Tn, &ctx->d_lnT, &ctx->d_E, &ctx->d_lnE, &ctx->d_src_cdf, &ctx->d_cell_cdf,
+                    &ctx->d_spec_nud, &ctx->d_teff, &ctx->d_unu, &ctx->d_uf, &ctx->d_T, &ctx->d_adot, &ctx->d_acc,
+                    &ctx->d_sed, &ctx->d_img})
+        b->release();
+    ctx->d_uoff.release(); ctx->d_un.release(); ctx->d_img_bin.release(); ctx->d_row.release();
+    ctx->d_keys.release(); ctx->d_esc.release(); ctx->d_counters.release(); ctx->d_state.release();
+    ctx->d_hist.release(); ctx->d_abort.release(); ctx->d_work.release();
+    if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
+    for (auto e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    return HRT_OK;
+}
+
+const char* hrt_last_error(const hrt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int hrt_set_stream(hrt_ctx* ctx, void* stream) {
+    if (!ctx) return HRT_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return HRT_OK;
+}
+
+static int set_grid(hrt_ctx* ctx, int type, int n1, int n2, int n3, const double* w1, const double* w2, const double* w3) {
+    if (!ctx) return HRT_EINVAL;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || !w1 || !w2 || !w3) return ctx->fail(HRT_EINVAL, "grid: empty axis");
+    if ((int64_t)n1 * n2 * n3 >= (int64_t)1 << 31) return ctx->fail(HRT_EINVAL, "grid: more than 2^31 cells");
+    const double* w[3] = {w1, w2, w3};
+    const int n[3] = {n1, n2, n3};
+    for (int a = 0; a < 3; ++a)
+        if (!finite_all(w[a], n[a] + 1) || !increasing(w[a], n[a] + 1))
+            return ctx->fail(HRT_EINVAL, "grid: walls of axis %d not finite and strictly increasing", a);
+    if (type == GRID_SPHERICAL) {
+        if (w1[0] < 0) return ctx->fail(HRT_EINVAL, "grid: negative radius");
+        if (w2[0] != 0.0 || std::fabs(w2[n2] - PI) > 1e-12) return ctx->fail(HRT_EINVAL, "grid: theta walls must span [0, pi]");
+        if (w3[0] != 0.0 || std::fabs(w3[n3] - 2 * PI) > 1e-12) return ctx->fail(HRT_EINVAL, "grid: phi walls must span [0, 2 pi]");
+        if (n3 > 1)
+            for (int k = 0; k < n3; ++k)
+                if (w3[k + 1] - w3[k] > PI + 1e-12) return ctx->fail(HRT_EINVAL, "grid: phi cells wider than pi");
+    }
+    ctx->gtype = type;
+    double L0 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        ctx->n[a] = n[a];
+        ctx->w[a].assign(w[a], w[a] + n[a] + 1);
+        if (type == GRID_CARTESIAN || a == 0)
+            L0 = std::max(L0, std::max(std::fabs(w[a][0]), std::fabs(w[a][n[a]])));
+    }
+    if (type == GRID_SPHERICAL) {
+        ctx->w[1].back() = PI;
+        ctx->w[2].back() = 2 * PI;
+    }
+    ctx->L0 = L0 > 0 ? L0 : 1.0;
+    ctx->rho.clear();
+    ctx->Lcell.clear();
+    ctx->have_T = false;
+    ctx->have_Q = false;
+    ctx->dirty_grid = ctx->dirty_src = ctx->dirty_obs = true;
+    return HRT_OK;
+}
+
+int hrt_set_grid_cartesian(hrt_ctx* ctx, int nx, int ny, int nz, const double* xw, const double* yw, const double* zw) {
+    return set_grid(ctx, GRID_CARTESIAN, nx, ny, nz, xw, yw, zw);
+}
+
+int hrt_set_grid_spherical(hrt_ctx* ctx, int nr, int nt, int np, const double* rw, const double* tw, const double* pw) {
+    return set_grid(ctx, GRID_SPHERICAL, nr, nt, np, rw, tw, pw);
+}
+
+int hrt_set_density(hrt_ctx* ctx, const float* rho, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "density before grid");
+    if (!rho || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "density: expected %lld cells", (long long)ctx->ncells());
+    int64_t nd = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        if (!std::isfinite(rho[c]) || rho[c] < 0.f) return ctx->fail(HRT_EINVAL, "density: cell %lld not finite and >= 0", (long long)c);
+        nd += rho[c] > 0.f;
+    }
+    ctx->rho.assign(rho, rho + n);
+    ctx->n_dust = nd;
+    ctx->dirty_grid = true;
+    return HRT_OK;
+}
+
+int hrt_set_dust(hrt_ctx* ctx, int nnu, const double* nu, const double* chi, const double* albedo, double g, int nT,
+                 const double* T) {
+    if (!ctx) return HRT_EINVAL;
+    if (nnu < 2 || nT < 2 || !nu || !chi || !albedo || !T) return ctx->fail(HRT_EINVAL, "dust: need >= 2 nodes");
+    if (!finite_all(nu, nnu) || !increasing(nu, nnu) || nu[0] <= 0) return ctx->fail(HRT_EINVAL, "dust: nu must increase");
+    for (int k = 0; k < nnu; ++k)
+        if (!(chi[k] > 0) || !std::isfinite(chi[k]) || !(albedo[k] >= 0 && albedo[k] <= 1))
+            return ctx->fail(HRT_EINVAL, "dust: chi > 0 and albedo in [0,1] required (node %d)", k);
+    if (!(g > -1 && g < 1)) return ctx->fail(HRT_EINVAL, "dust: g outside (-1, 1)");
+    if (!finite_all(T, nT) || !increasing(T, nT) || T[0] <= 0) return ctx->fail(HRT_EINVAL, "dust: T nodes must increase");
+    ctx->nu.assign(nu, nu + nnu);
+    ctx->chi.assign(chi, chi + nnu);
+    ctx->alb.assign(albedo, albedo + nnu);
+    ctx->Tn.assign(T, T + nT);
+    ctx->g = g;
+    ctx->dirty_dust = true;
+    ctx->dirty_src = true;
+    return HRT_OK;
+}
+
+static int add_point(hrt_ctx* ctx, const double x[3], double L, double teff, int n, const double* nu, const double* f) {
+    if (!ctx) return HRT_EINVAL;
+    if (!x || !finite_all(x, 3)) return ctx->fail(HRT_EINVAL, "source: position not finite");
+    if (!(L > 0) || !std::isfinite(L)) return ctx->fail(HRT_EINVAL, "source: L must be > 0");
+    if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "source before grid");
+    if (ctx->gtype == GRID_CARTESIAN) {
+        for (int a = 0; a < 3; ++a)
+            if (x[a] < ctx->w[a].front() || x[a] > ctx->w[a].back()) return ctx->fail(HRT_EINVAL, "source outside the grid");
+    } else if (std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) >= ctx->w[0].back()) {
+        return ctx->fail(HRT_EINVAL, "source outside the grid");
+    }
+    PointSrc p;
+    for (int a = 0; a < 3; ++a) p.x[a] = x[a];
+    p.L = L;
+    p.teff = teff;
+    if (n > 0) {
+        if (!nu || !f || n < 2 || !increasing(nu, n) || !finite_all(f, n)) return ctx->fail(HRT_EINVAL, "source spectrum");
+        for (int k = 0; k < n; ++k)
+            if (f[k] < 0) return ctx->fail(HRT_EINVAL, "source spectrum negative");
+        p.unu.assign(nu, nu + n);
+        p.uf.assign(f, f + n);
+    } else if (!(teff > 0)) {
+        return ctx->fail(HRT_EINVAL, "source: Teff must be > 0");
+    }
+    ctx->pts.push_back(p);
+    ctx->dirty_src = true;
+    return HRT_OK;
+}
+
+int hrt_add_point_source(hrt_ctx* ctx, const double x[3], double L, double Teff) {
+    return add_point(ctx, x, L, Teff, 0, nullptr, nullptr);
+}
+
+int hrt_add_point_source_spectrum(hrt_ctx* ctx, const double x[3], double L, int n, const double* nu, const double* fnu) {
+    if (n < 2) return ctx ? ctx->fail(HRT_EINVAL, "source spectrum needs >= 2 nodes") : HRT_EINVAL;
+    return add_point(ctx, x, L, 0.0, n, nu, fnu);
+}
+
+int hrt_set_cell_source(hrt_ctx* ctx, const double* Lcell, int64_t n, double Teff) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "cell source before grid");
+    if (!Lcell || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "cell source: expected %lld cells", (long long)ctx->ncells());
+    if (!(Teff > 0)) return ctx->fail(HRT_EINVAL, "cell source: Teff must be > 0");
+    double tot = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+        if (!(Lcell[c] >= 0) || !std::isfinite(Lcell[c])) return ctx->fail(HRT_EINVAL, "cell source: L must be finite >= 0");
+        tot += Lcell[c];
+    }
+    if (!(tot > 0)) return ctx->fail(HRT_EINVAL, "cell source: zero luminosity");
+    ctx->Lcell.assign(Lcell, Lcell + n);
+    ctx->cell_teff = Teff;
+    ctx->dirty_src = true;
+    return HRT_OK;
+}
+
+int hrt_clear_sources(hrt_ctx* ctx) {
+    if (!ctx) return HRT_EINVAL;
+    ctx->pts.clear();
+    ctx->Lcell.clear();
+    ctx->dirty_src = true;
+    return HRT_OK;
+}
+
+int hrt_set_peeloff(hrt_ctx* ctx, int nobs, const double* incl, const double* az, int nsed, double lam_min_um,
+                    double lam_max_um, int img_nx, int img_ny, double img_half_extent_cm, int nimg, const double* img_lam_um) {
+    if (!ctx) return HRT_EINVAL;
+    if (nobs < 0 || (nobs > 0 && (!incl || !az))) return ctx->fail(HRT_EINVAL, "peeloff: observers");
+    if (nsed < 1 || !(lam_min_um > 0) || !(lam_max_um > lam_min_um)) return ctx->fail(HRT_EINVAL, "peeloff: SED bins");
+    if (img_nx < 0 || img_ny < 0 || (img_nx > 0 && (img_ny < 1 || !(img_half_extent_cm > 0) || nimg < 1 || !img_lam_um)))
+        return ctx->fail(HRT_EINVAL, "peeloff: image");
+    if (nobs > 0 && (!finite_all(incl, nobs) || !finite_all(az, nobs))) return ctx->fail(HRT_EINVAL, "peeloff: angles");
+    ctx->nobs = nobs;
+    ctx->incl.assign(incl, incl + nobs);
+    ctx->az.assign(az, az + nobs);
+    ctx->nsed = nsed;
+    ctx->lam_min_um = lam_min_um;
+    ctx->lam_max_um = lam_max_um;
+    ctx->img_nx = img_nx;
+    ctx->img_ny = img_ny;
+    ctx->img_half = img_half_extent_cm;
+    ctx->nimg = img_nx > 0 ? nimg : 0;
+    ctx->img_lam.assign(img_lam_um, img_lam_um + ctx->nimg);
+    ctx->dirty_obs = true;
+    return HRT_OK;
+}
+
+void hrt_default_params(hrt_run_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->max_interactions = 1000000;
+    p->peel = 0;
+    p->update_temperature = 1;
+    p->terminate_on_absorb = 0;
+    p->quantity = 0;
+    p->p = 0.99;
+    p->q_thres = 1.02;
+    p->delta_thres = std::numeric_limits<double>::infinity();
+    p->kernel = HRT_KERNEL_EVENT;
+    p->watchdog_ms = 0.0;
+}
+
+int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* params, hrt_iter_stats* out) {
+    if (!ctx) return HRT_EINVAL;
+    hrt_run_params P;
+    if (params) P = *params;
+    else hrt_default_params(&P);
+    if (n_packets < 1 || n_packets > 0xFFFFFFFFll) return ctx->fail(HRT_EINVAL, "n_packets must be in [1, 2^32)");
+    if (!(P.p > 0 && P.p <= 1)) return ctx->fail(HRT_EINVAL, "percentile p must be in (0, 1]");
+    if (P.max_interactions < 0) return ctx->fail(HRT_EINVAL, "max_interactions < 0");
+    DeviceGuard dg(ctx->device);
+    int rc = prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    const cudaStream_t s = ctx->stream;
+    const int64_t nc = ctx->ncells();
+    int launched = 0;
+    CK(cudaEventRecord(ctx->ev[0], s), "event");
+    if (P.update_temperature) {
+        CK(cudaMemsetAsync(ctx->d_acc.p, 0, nc * sizeof(double), s), "zero acc");
+        CK(launch_emit_rows(ctx->d_T.p, ctx->d_row.p, nc, ctx->d_lnT.p, (int)ctx->Tn.size(), s), "emission rows");
+        launched++;
+    }
+    if (P.peel) {
+        CK(cudaMemsetAsync(ctx->d_sed.p, 0, ctx->d_sed.n * sizeof(double), s), "zero sed");
+        CK(cudaMemsetAsync(ctx->d_img.p, 0, ctx->d_img.n * sizeof(double), s), "zero image");
+    }
+    CK(cudaMemsetAsync(ctx->d_esc.p, 0, ctx->d_esc.n * sizeof(unsigned long long), s), "zero escape");
+    CK(cudaMemsetAsync(ctx->d_counters.p, 0, ctx->d_counters.n * sizeof(unsigned long long), s), "zero counters");
+    CK(cudaMemsetAsync(ctx->d_abort.p, 0, sizeof(int32_t), s), "zero abort");
+    CK(cudaMemsetAsync(ctx->d_work.p, 0, ctx->d_work.n * sizeof(unsigned long long), s), "zero work");
+
+    PropagateJob job;
+    job.grid = ctx->grid;
+    job.dust = ctx->dust;
+    job.src = ctx->src;
+    job.obs = ctx->obs;
+    // the acc buffer is written only by Lucy iterations; an imaging pass writes a scratch copy
+    job.tal.acc = ctx->d_acc.p;
+    job.tal.sed = ctx->d_sed.p;
+    job.tal.img = ctx->d_img.p;
+    job.tal.esc = ctx->d_esc.p;
+    job.tal.counters = ctx->d_counters.p;
+    job.tal.abort_flag = ctx->d_abort.p;
+    RunArgs& A = job.args;
+    A = RunArgs{};
+    A.n_packets = n_packets;
+    A.first_packet = 0;
+    A.key0 = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
+    A.key1 = (uint32_t)(ctx->seed >> 32);
+    A.iter_key = P.update_temperature ? (uint32_t)ctx->iteration : (0x80000000u | (uint32_t)ctx->iteration);
+    A.model_key = ctx->model_id;
+    A.eps = ctx->L_tot / (double)n_packets;
+    ctx->last_eps = A.eps;
+    A.epsL0 = A.eps * ctx->L0;
+    A.max_interactions = P.max_interactions;
+    A.peel = P.peel && ctx->nobs > 0;
+    A.terminate_on_absorb = P.terminate_on_absorb;
+    A.budget_ns = P.watchdog_ms > 0 ? (uint64_t)(P.watchdog_ms * 1e6) : 0ull;
+    A.smem_sed = (size_t)ctx->obs.nobs * ctx->obs.nsed * 8 + (size_t)N_ESC_MU * ctx->obs.nsed * 4 <= 96 * 1024;
+    A.work_counter = ctx->d_work.p;
+    A.t0 = ctx->d_work.p + 1;
+    Launch L;
+    L.block = P.block_size > 0 ? P.block_size : 256;
+    L.blocks_per_sm = P.blocks_per_sm;
+    L.regroup = P.regroup_threshold;
+    if (!P.update_temperature) {
+        // imaging pass: deposits go to a scratch buffer (the key buffer), the Lucy accumulators are kept
+        job.tal.acc = reinterpret_cast<double*>(ctx->d_keys.p);
+        CK(cudaMemsetAsync(ctx->d_keys.p, 0, nc * sizeof(double), s), "zero scratch");
+    }
+    CK(launch_stamp(ctx->d_work.p + 1, s), "stamp");
+    launched++;
+    cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
+                                                 : launch_propagate_event(job, L, s, &launched);
+    CK(e, "propagate");
+    CK(cudaEventRecord(ctx->ev[1], s), "event");
+    const int64_t k_rank = ctx->n_dust > 0 ? (nc - ctx->n_dust) + (int64_t)std::ceil(P.p * (double)ctx->n_dust) - 1 : 0;
+    if (P.update_temperature) {
+        TemperatureJob tj;
+        tj.gtype = ctx->gtype;
+        tj.n1 = ctx->n[0]; tj.n2 = ctx->n[1]; tj.n3 = ctx->n[2];
+        tj.ncells = nc;
+        tj.rhoL = ctx->d_rhoL.p;
+        tj.acc = ctx->d_acc.p;
+        tj.va = ctx->d_va.p; tj.vb = ctx->d_vb.p; tj.vc = ctx->d_vc.p;
+        tj.E = ctx->d_E.p; tj.lnE = ctx->d_lnE.p; tj.lnT = ctx->d_lnT.p; tj.Tn = ctx->d_Tn.p;
+        tj.nT = (int)ctx->Tn.size();
+        tj.quantity = P.quantity;
+        tj.first = ctx->iteration == 0 ? 1 : 0;
+        tj.T = ctx->d_T.p;
+        tj.adot = ctx->d_adot.p;
+        tj.emit_row = ctx->d_row.p;
+        tj.keys = ctx->d_keys.p;
+        tj.counters = ctx->d_counters.p + N_COUNTERS;
+        CK(launch_temperature(tj, s, &launched), "temperature");
+        if (ctx->n_dust > 0) {
+            int kk = std::max<int64_t>(0, std::min<int64_t>(k_rank, nc - 1));
+            CK(launch_select_kth(ctx->d_keys.p, nc, (unsigned long long)kk, ctx->d_hist.p, ctx->d_state.p,
+                                 ctx->d_counters.p + N_COUNTERS + 2, s, &launched),
+               "quantile");
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_counters.p, sizeof(unsigned long long) * (N_COUNTERS + 4),
+                       cudaMemcpyDeviceToHost, s),
+       "stats copy");
+    CK(cudaEventRecord(ctx->ev[2], s), "event");
+    CK(cudaStreamSynchronize(s), "iteration");
+    const unsigned long long* h = ctx->h_stats;
+    hrt_iter_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.iteration = ctx->iteration;
+    st.n_packets = n_packets;
+    st.e_emitted = ctx->L_tot;
+    st.e_escaped = (double)h[C_ESCAPED] * A.eps;
+    st.e_killed = (double)h[C_KILLED] * A.eps;
+    st.e_absorbed = (double)h[C_ABSORBED_TERM] * A.eps;
+    st.n_interactions = (int64_t)h[C_INTERACTIONS];
+    st.n_scatter = (int64_t)h[C_SCATTER];
+    st.n_absorb = (int64_t)h[C_ABSORB];
+    st.n_crossings = (int64_t)h[C_CROSSINGS];
+    st.n_peel_crossings = (int64_t)h[C_PEEL_CROSSINGS];
+    st.n_killed = (int64_t)h[C_KILLED];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    st.ms_propagate = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
+    st.ms_total = ms;
+    st.kernel_launches = launched;
+    const double inf = std::numeric_limits<double>::infinity();
+    st.Q = inf;
+    st.Delta = inf;
+    if (P.update_temperature) {
+        st.clamp_low = (int64_t)h[N_COUNTERS];
+        st.clamp_high = (int64_t)h[N_COUNTERS + 1];
+        if (ctx->n_dust > 0) {
+            unsigned long long key = h[N_COUNTERS + 2];
+            double Q;
+            std::memcpy(&Q, &key, sizeof(Q));
+            st.Q = Q;
+            st.Delta = ctx->have_Q && std::isfinite(ctx->Q_prev) && std::isfinite(Q)
+                           ? std::max(ctx->Q_prev / Q, Q / ctx->Q_prev)
+                           : inf;
+            ctx->Q_prev = Q;
+            ctx->have_Q = true;
+        }
+        st.converged = (st.Q < P.q_thres) && (st.Delta < P.delta_thres || std::isinf(P.delta_thres)) ? 1 : 0;
+        ctx->iteration++;
+    }
+    if (out) *out = st;
+    if (h[C_WATCHDOG] > 0) return ctx->fail(HRT_ETIMEDOUT, "propagation watchdog expired after %.3f ms", P.watchdog_ms);
+    return HRT_OK;
+}
+
+// ---------------------------------------------------------------- read-out / state
+static int get_dev(hrt_ctx* ctx, const void* src, size_t bytes_avail, void* dst, size_t bytes, bool to_host) {
+    if (!dst) return ctx->fail(HRT_EINVAL, "null output");
+    if (bytes > bytes_avail || !src) return ctx->fail(HRT_ESTATE, "nothing to read (run an iteration first)");
+    DeviceGuard dg(ctx->device);
+    CK(cudaMemcpyAsync(dst, src, bytes, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    if (to_host) CK(cudaStreamSynchronize(ctx->stream), "copy");
+    return HRT_OK;
+}
+
+int64_t hrt_num_cells(const hrt_ctx* ctx) { return ctx ? ctx->ncells() : -1; }
+
+int hrt_get_temperature(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (n < ctx->ncells()) return ctx->fail(HRT_EINVAL, "output shorter than the cell count");
+    return get_dev(ctx, ctx->d_T.p, ctx->d_T.n * 8, out, ctx->ncells() * 8, true);
+}
+int hrt_get_temperature_device(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (n < ctx->ncells()) return ctx->fail(HRT_EINVAL, "output shorter than the cell count");
+    return get_dev(ctx, ctx->d_T.p, ctx->d_T.n * 8, out, ctx->ncells() * 8, false);
+}
+int hrt_get_specific_energy(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (n < ctx->ncells()) return ctx->fail(HRT_EINVAL, "output shorter than the cell count");
+    return get_dev(ctx, ctx->d_adot.p, ctx->d_adot.n * 8, out, ctx->ncells() * 8, true);
+}
+int hrt_get_absorbed(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (n < ctx->ncells()) return ctx->fail(HRT_EINVAL, "output shorter than the cell count");
+    return get_dev(ctx, ctx->d_acc.p, ctx->d_acc.n * 8, out, ctx->ncells() * 8, true);
+}
+int hrt_get_sed(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    const int64_t m = (int64_t)ctx->nobs * ctx->nsed;
+    if (n < m) return ctx->fail(HRT_EINVAL, "output shorter than nobs*nsed");
+    return get_dev(ctx, ctx->d_sed.p, ctx->d_sed.n * 8, out, m * 8, true);
+}
+int hrt_get_sed_device(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    const int64_t m = (int64_t)ctx->nobs * ctx->nsed;
+    if (n < m) return ctx->fail(HRT_EINVAL, "output shorter than nobs*nsed");
+    return get_dev(ctx, ctx->d_sed.p, ctx->d_sed.n * 8, out, m * 8, false);
+}
+int hrt_get_image(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    const int64_t m = (int64_t)ctx->nobs * ctx->nimg * ctx->img_nx * ctx->img_ny;
+    if (n < m) return ctx->fail(HRT_EINVAL, "output shorter than the image");
+    if (m == 0) return HRT_OK;
+    return get_dev(ctx, ctx->d_img.p, ctx->d_img.n * 8, out, m * 8, true);
+}
+int hrt_get_escape(hrt_ctx* ctx, double* out, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    const int64_t m = (int64_t)N_ESC_MU * ctx->nsed;
+    if (n < m) return ctx->fail(HRT_EINVAL, "output shorter than 10*nsed");
+    std::vector<unsigned long long> cnt(m);
+    int rc = get_dev(ctx, ctx->d_esc.p, ctx->d_esc.n * 8, cnt.data(), m * 8, true);
+    if (rc != HRT_OK) return rc;
+    // counts of escaping packets times the packet energy of the last call
+    for (int64_t i = 0; i < m; ++i) out[i] = (double)cnt[i] * ctx->last_eps;
+    return HRT_OK;
+}
+
+int hrt_set_temperature(hrt_ctx* ctx, const double* T, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0 || (int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "set grid and density first");
+    if (!T || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "temperature: expected %lld cells", (long long)ctx->ncells());
+    for (int64_t c = 0; c < n; ++c)
+        if (!(T[c] > 0) || !std::isfinite(T[c])) return ctx->fail(HRT_EINVAL, "temperature must be finite > 0");
+    DeviceGuard dg(ctx->device);
+    if (ctx->dirty_grid) {
+        int rc = stage_grid(ctx);
+        if (rc != HRT_OK) return rc;
+    }
+    CK(ctx->d_T.upload(T, n, ctx->stream), "upload T");
+    CK(cudaStreamSynchronize(ctx->stream), "upload T");
+    ctx->have_T = true;
+    return HRT_OK;
+}
+
+int hrt_set_temperature_device(hrt_ctx* ctx, const double* d_T, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0 || (int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "set grid and density first");
+    if (!d_T || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "temperature: expected %lld cells", (long long)ctx->ncells());
+    DeviceGuard dg(ctx->device);
+    if (ctx->dirty_grid) {
+        int rc = stage_grid(ctx);
+        if (rc != HRT_OK) return rc;
+    }
+    CK(cudaMemcpyAsync(ctx->d_T.p, d_T, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "copy T");
+    ctx->have_T = true;
+    return HRT_OK;
+}
+
+int hrt_set_iteration(hrt_ctx* ctx, int iteration) {
+    if (!ctx || iteration < 0) return HRT_EINVAL;
+    ctx->iteration = iteration;
+    return HRT_OK;
+}
+
+int hrt_set_model_id(hrt_ctx* ctx, uint32_t model_id) {
+    if (!ctx) return HRT_EINVAL;
+    ctx->model_id = model_id;
+    return HRT_OK;
+}
+
+// ---------------------------------------------------------------- single steps
+int hrt_step_philox(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, void* stream) {
+    if (n < 0 || (n > 0 && (!d_ctr || !d_key || !d_out))) return HRT_EINVAL;
+    cudaError_t e = launch_step_philox(n, d_ctr, d_key, d_out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? HRT_OK : HRT_ECUDA;
+}
+
+static int step_prepare(hrt_ctx* ctx) {
+    if (!ctx) return HRT_EINVAL;
+    DeviceGuard dg(ctx->device);
+    return prepare(ctx);
+}
+
+int hrt_step_cell_exit(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir, const int32_t* d_cell,
+                       float* d_dist, int32_t* d_exit) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_cell_exit(ctx->grid, n, d_pos, d_dir, d_cell, d_dist, d_exit, (float)(1.0 / ctx->L0), (float)ctx->L0,
+                             ctx->stream),
+       "cell exit");
+    CK(cudaStreamSynchronize(ctx->stream), "cell exit");
+    return HRT_OK;
+}
+
+int hrt_step_tau_to_edge(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir, const float* d_nu, float* d_tau) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_tau(ctx->grid, ctx->dust, n, d_pos, d_dir, d_nu, d_tau, (float)(1.0 / ctx->L0), ctx->stream), "tau");
+    CK(cudaStreamSynchronize(ctx->stream), "tau");
+    return HRT_OK;
+}
+
+int hrt_step_hg_scatter(hrt_ctx* ctx, int64_t n, const float* d_dir_in, const float* d_u1, const float* d_u2,
+                        float* d_dir_out) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->nu.empty()) return ctx->fail(HRT_ESTATE, "dust not set");
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_hg((float)ctx->g, n, d_dir_in, d_u1, d_u2, d_dir_out, ctx->stream), "hg");
+    CK(cudaStreamSynchronize(ctx->stream), "hg");
+    return HRT_OK;
+}
+
+int hrt_step_sample_emission(hrt_ctx* ctx, int64_t n, const int32_t* d_row, const float* d_u, float* d_nu) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_sample(ctx->dust.nu, ctx->dust.cdf_emit, ctx->dust.nnu, n, d_row, d_u, d_nu, ctx->stream), "sample");
+    CK(cudaStreamSynchronize(ctx->stream), "sample");
+    return HRT_OK;
+}
+
+int hrt_step_sample_source(hrt_ctx* ctx, int64_t n, const int32_t* d_src, const float* d_u, float* d_nu) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_sample(ctx->src.spec_nu, ctx->src.spec_cdf, ctx->src.nspec, n, d_src, d_u, d_nu, ctx->stream), "sample");
+    CK(cudaStreamSynchronize(ctx->stream), "sample");
+    return HRT_OK;
+}
+
+int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* d_T) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    CK(launch_invert_temperature(d_adot, d_T, n, ctx->d_E.p, ctx->d_lnE.p, ctx->d_lnT.p, ctx->d_Tn.p,
+                                 (int)ctx->Tn.size(), ctx->stream),
+       "temperature");
+    CK(cudaStreamSynchronize(ctx->stream), "temperature");
+    return HRT_OK;
+}
+
+int hrt_get_tables(hrt_ctx* ctx, double* E, int64_t nE, float* cdf, int64_t ncdf) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    const int64_t nT = (int64_t)ctx->Tn.size(), nnu = (int64_t)ctx->nu.size();
+    if (nE < nT || ncdf < nT * nnu || !E || !cdf) return ctx->fail(HRT_EINVAL, "table outputs too short");
+    DeviceGuard dg(ctx->device);
+    CK(cudaMemcpyAsync(E, ctx->d_E.p, nT * 8, cudaMemcpyDeviceToHost, ctx->stream), "tables");
+    CK(cudaMemcpyAsync(cdf, ctx->d_cdf_emit.p, nT * nnu * 4, cudaMemcpyDeviceToHost, ctx->stream), "tables");
+    CK(cudaStreamSynchronize(ctx->stream), "tables");
+    return HRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Host-side declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hrt_types.h"
+
+namespace hrt {
+
+// Launch shape of a propagation kernel.
+struct Launch {
+    int block = 256;
+    int blocks = 0;          // 0: blocks_per_sm * SMs
+    int blocks_per_sm = 0;   // 0: occupancy limit
+    int regroup = 0;         // event kernel regroup threshold (lanes)
+};
+
+// Device-side view of one model plus the launch parameters of one propagation pass.
+struct PropagateJob {
+    DevGrid grid;
+    DevDust dust;
+    DevSources src;
+    DevObs obs;
+    Tallies tal;
+    RunArgs args;
+};
+
+// propagate.cu
+cudaError_t launch_stamp(unsigned long long* t0, cudaStream_t s);
+cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
+cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
+
+// temperature.cu
+struct TemperatureJob {
+    int32_t gtype;
+    int32_t n1, n2, n3;
+    int64_t ncells;
+    const float* rhoL;
+    const double* acc;
+    const double* va;    // per-axis volume factors: V = va[i] vb[j] vc[k] (cm^3)
+    const double* vb;
+    const double* vc;
+    const double* E;     // [nT] emission table
+    const double* lnE;   // [nT]
+    const double* lnT;   // [nT]
+    const double* Tn;    // [nT]
+    int32_t nT;
+    int32_t quantity;    // 0 T, 1 Adot
+    int32_t first;       // first iteration for the Adot quantity (no previous value)
+    double* T;           // in: previous, out: new
+    double* adot;        // in: previous, out: new
+    int32_t* emit_row;   // out
+    unsigned long long* keys;       // out: bit pattern of R (0 for cells without dust)
+    unsigned long long* counters;   // [2] clamp low/high (cells with dust)
+};
+cudaError_t launch_temperature(const TemperatureJob& j, cudaStream_t s, int* launched);
+// exact nearest-rank select of the k-th smallest key; writes the key to *d_out
+cudaError_t launch_select_kth(const unsigned long long* keys, int64_t n, unsigned long long k,
+                              unsigned int* d_hist, unsigned long long* d_state, unsigned long long* d_out,
+                              cudaStream_t s, int* launched);
+cudaError_t launch_invert_temperature(const double* adot, double* T, int64_t n, const double* E, const double* lnE,
+                                      const double* lnT, const double* Tn, int nT, cudaStream_t s);
+cudaError_t launch_emit_rows(const double* T, int32_t* rows, int64_t n, const double* lnT, int nT, cudaStream_t s);
+
+// tables.cu (FP64 table construction on the device)
+cudaError_t launch_emission_tables(int nnu, const double* nu, const double* kappa, int nT, const double* T,
+                                   double* E, double* lnE, float* cdf, cudaStream_t s);
+cudaError_t launch_source_spectra(int nsrc, int nspec, const double* spec_nu, const double* teff,
+                                  const double* user_nu, const double* user_f, const int* user_off,
+                                  const int* user_n, float* spec_cdf, cudaStream_t s);
+
+// steps.cu
+cudaError_t launch_step_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out, cudaStream_t s);
+cudaError_t launch_step_cell_exit(const DevGrid& g, int64_t n, const float* pos, const float* dir,
+                                  const int32_t* cell, float* dist, int32_t* ex, float inv_L0, float L0, cudaStream_t s);
+cudaError_t launch_step_tau(const DevGrid& g, const DevDust& d, int64_t n, const float* pos, const float* dir,
+                            const float* nu, float* tau, float inv_L0, cudaStream_t s);
+cudaError_t launch_step_hg(float g, int64_t n, const float* din, const float* u1, const float* u2, float* dout,
+                           cudaStream_t s);
+cudaError_t launch_step_sample(const float* x, const float* cdf, int nx, int64_t n, const int32_t* row,
+                               const float* u, float* out, cudaStream_t s);
+
+}  // namespace hrt

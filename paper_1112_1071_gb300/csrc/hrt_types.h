@@ -1,0 +1,120 @@
+// Plain structs handed to the kernels by value: device views of the problem (grid, dust,
+// sources, observers), the per-call arguments and the output tallies.  Lengths are in the
+// scaled unit L0 (the grid's largest |coordinate| or outer radius), so positions are O(1).
+#pragma once
+#include <cstdint>
+
+namespace hrt {
+
+enum GridType : int32_t { GRID_CARTESIAN = 0, GRID_SPHERICAL = 1 };
+
+struct DevGrid {
+    int32_t type;
+    int32_t n1, n2, n3;            // cells per axis (x,y,z) or (r,theta,phi)
+    int64_t ncells;
+    const float* rhoL;             // [ncells] rho * L0 (so dtau = rhoL * chi * l)
+    // Cartesian walls (scaled)
+    const float* w1;
+    const float* w2;
+    const float* w3;
+    // spherical: radii (scaled) and squares, polar walls (angle, cos, sin), azimuthal walls
+    const float* rw;               // [n1+1]
+    const float* r2w;              // [n1+1]
+    const double* rwd;             // [n1+1] FP64 radii for small-r solves
+    const float* thw;              // [n2+1]
+    const float* cth;              // [n2+1] cos, exactly 0 for the midplane wall
+    const float* sth;
+    const double* cthd;            // FP64 copies for near-axis cones
+    const double* sthd;
+    const float* phw;              // [n3+1]
+    const float* cph;
+    const float* sph;
+    float r0;                      // inner radius (scaled), 0 without a hole
+    float r_fp64;                  // sphere solves for walls below this radius run in FP64
+    float sin_fp64;                // cone solves for walls with sin(theta) below this run in FP64
+    int32_t pad0;
+};
+
+struct DevDust {
+    int32_t nnu;
+    int32_t nT;
+    const float* lnu;              // [nnu] ln nu
+    const float* inv_dlnu;         // [nnu-1] 1/(ln nu_{j+1} - ln nu_j)
+    const float* lchi;             // [nnu] ln chi
+    const float* alb;              // [nnu]
+    const float* nu;               // [nnu]
+    const float* cdf_emit;         // [nT][nnu] cumulative emissivity rows
+    const int32_t* emit_row;       // [ncells] row used for re-emission in this iteration
+    float g;
+    int32_t pad0;
+};
+
+struct DevSources {
+    int32_t npoint;
+    int32_t nsrc;                  // npoint + (cell source ? 1 : 0)
+    int32_t nspec;                 // spectrum nodes per source
+    int32_t pad0;
+    const float* pos;              // [npoint][3] scaled
+    const double* cdf;             // [nsrc] cumulative luminosity
+    const float* spec_nu;          // [nspec]
+    const float* spec_cdf;         // [nsrc][nspec]
+    const double* cell_cdf;        // [ncells] cumulative cell luminosity or null
+};
+
+struct DevObs {
+    int32_t nobs;
+    int32_t nsed;
+    int32_t img_nx, img_ny, nimg;
+    int32_t pad0;
+    const float* n;                // [nobs][3]
+    const float* ex;               // [nobs][3]
+    const float* ey;               // [nobs][3]
+    double sed_a, sed_b;           // SED bin = floor(sed_a - sed_b * ln nu)
+    float img_scale;               // nx / (2 * half extent) in scaled units
+    float img_half;                // scaled half extent
+    const int32_t* img_bin;        // [nimg] SED bin per image wavelength
+};
+
+struct Tallies {
+    double* acc;                   // [ncells] sum eps kappa l (cgs)
+    double* sed;                   // [nobs][nsed]
+    double* img;                   // [nobs][nimg][ny][nx]
+    unsigned long long* esc;       // [10][nsed] escaping packet counts (x eps = energy)
+    unsigned long long* counters;  // [N_COUNTERS]
+    int32_t* abort_flag;           // set by the watchdog
+};
+
+enum Counter {
+    C_ESCAPED = 0,
+    C_KILLED,
+    C_ABSORBED_TERM,
+    C_INTERACTIONS,
+    C_SCATTER,
+    C_ABSORB,
+    C_CROSSINGS,
+    C_PEEL_CROSSINGS,
+    C_PACKETS_DONE,
+    C_WATCHDOG,
+    N_COUNTERS
+};
+
+constexpr int N_ESC_MU = 10;
+
+struct RunArgs {
+    int64_t n_packets;
+    int64_t first_packet;
+    uint32_t key0, key1;
+    uint32_t iter_key, model_key;
+    double eps;                    // packet energy (erg)
+    double epsL0;                  // eps * L0 (deposit per unit scaled length per kappa)
+    int64_t max_interactions;
+    int32_t peel;
+    int32_t terminate_on_absorb;
+    uint64_t budget_ns;            // watchdog budget after the launch stamp, 0 = none
+    int32_t regroup;               // event kernel: leave walk phase below this many walkers
+    int32_t smem_sed;              // 1: SED tallies in shared memory
+    unsigned long long* work_counter;   // event kernel: next packet to start
+    const unsigned long long* t0;  // globaltimer stamp written just before the launch
+};
+
+}  // namespace hrt

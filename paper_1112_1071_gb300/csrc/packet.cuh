@@ -1,0 +1,181 @@
+// Packet-level steps shared by the propagation kernels: emission (Sect. 2.1.1, 2.2), the walk
+// to a sampled optical depth with Lucy deposits (Sect. 2.2, Eq. 2), interactions (scatter or
+// absorb and re-emit, Sect. 2.2 and 2.1.3) and peeling-off (Sect. 2.6.2).
+#pragma once
+#include "device_grid.cuh"
+
+namespace hrt {
+
+struct LocalCounters {
+    unsigned long long v[N_COUNTERS];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < N_COUNTERS; ++i) v[i] = 0ull;
+    }
+};
+
+// Warp-reduce the per-thread counters and add them to the global tallies (one atomic per warp
+// and counter).
+__device__ __forceinline__ void flush_counters(const LocalCounters& lc, unsigned long long* g) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int i = 0; i < N_COUNTERS; ++i) {
+        unsigned long long x = lc.v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) atomicAdd(g + i, x);
+    }
+}
+
+// SED bin of a frequency: floor(nsed ln(lambda/lambda_min) / ln(lambda_max/lambda_min)), -1 outside.
+__device__ __forceinline__ int sed_bin(const DevObs& o, float nu) {
+    const double x = o.sed_a - o.sed_b * log((double)nu);
+    if (!(x >= 0.0) || x >= (double)o.nsed) return -1;
+    return (int)x;
+}
+
+struct Packet {
+    Ray r;
+    float nu;
+    DustAt dust;
+    int32_t sbin;
+    int64_t nint;
+    PacketRng rng;
+    float3 last_origin;      // emission position (before any hole crossing)
+    int32_t emit_relocate;   // 1: emission peel rays must locate their cell along the observer
+};
+
+__device__ __forceinline__ void set_frequency(Packet& pk, const DevDust& d, const DevObs& o, float nu) {
+    pk.nu = nu;
+    pk.dust = dust_at(d, nu);
+    pk.sbin = sed_bin(o, nu);
+}
+
+enum PeelKind : int32_t { PEEL_ISO = 0, PEEL_HG = 1 };
+
+// Peel-off towards every observer from position r.p: weight eps p exp(-tau_obs).  With
+// relocate, the starting cell is found along each observer direction (emission from a point
+// source, which may sit on walls or in the spherical hole); otherwise the packet's cell is used.
+template <int G>
+__device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, const RunArgs& a,
+                           const Tallies& t, double* sed_s, const Ray& at, float3 uin, int kind, bool relocate,
+                           float chi, int sbin, LocalCounters& lc) {
+    if (sbin < 0) return;
+    for (int ob = 0; ob < o.nobs; ++ob) {
+        const float3 n = make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2));
+        const float prob = (kind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
+        Ray pr = at;
+        set_dir(pr, n);
+        float tau = 0.f;
+        bool inside = true;
+        if (relocate) inside = grid_locate<G>(g, pr);
+        if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], F_INF);
+        const double w = a.eps * (double)(prob * expf(-tau));
+        if (sed_s) atomicAdd(sed_s + ob * o.nsed + sbin, w);
+        else atomicAdd(t.sed + (int64_t)ob * o.nsed + sbin, w);
+        if (o.nimg > 0) {
+            const float px = at.p.x * __ldg(o.ex + 3 * ob) + at.p.y * __ldg(o.ex + 3 * ob + 1) + at.p.z * __ldg(o.ex + 3 * ob + 2);
+            const float py = at.p.x * __ldg(o.ey + 3 * ob) + at.p.y * __ldg(o.ey + 3 * ob + 1) + at.p.z * __ldg(o.ey + 3 * ob + 2);
+            const int ix = (int)floorf((px + o.img_half) * o.img_scale);
+            const int iy = (int)floorf((py + o.img_half) * o.img_scale);
+            if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny) {
+                for (int l = 0; l < o.nimg; ++l) {
+                    if (__ldg(o.img_bin + l) != sbin) continue;
+                    atomicAdd(t.img + (((int64_t)ob * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
+                }
+            }
+        }
+    }
+}
+
+// Emission: source by luminosity CDF, then position (cell sources), direction, frequency.
+// Returns false when the packet starts outside the grid (counted as escaped).
+template <int G>
+__device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources& s, const DevObs& o,
+                            const RunArgs& a, const Tallies& t, double* sed_s, int64_t pid, Packet& pk,
+                            LocalCounters& lc, bool inline_peel = true) {
+    pk.rng.init(make_uint2(a.key0, a.key1), (uint32_t)pid, a.iter_key, a.model_key);
+    pk.nint = 0;
+    const int src = (int)select_cdf<double>(s.cdf, s.nsrc, (double)pk.rng.next());
+    if (src < s.npoint) {
+        pk.r.p = make_float3(__ldg(s.pos + 3 * src), __ldg(s.pos + 3 * src + 1), __ldg(s.pos + 3 * src + 2));
+        const float u1 = pk.rng.next(), u2 = pk.rng.next();
+        set_dir(pk.r, isotropic_dir(u1, u2));
+        set_frequency(pk, d, o, sample_table(s.spec_nu, s.spec_cdf + (int64_t)src * s.nspec, s.nspec, pk.rng.next()));
+        const Ray at = pk.r;
+        pk.last_origin = at.p;
+        pk.emit_relocate = 1;
+        if (!grid_locate<G>(g, pk.r)) return false;
+        if (a.peel && inline_peel) peel_event<G>(g, d, o, a, t, sed_s, at, pk.r.u, PEEL_ISO, true, pk.dust.chi, pk.sbin, lc);
+    } else {
+        pk.emit_relocate = 0;
+        const int64_t c = select_cdf<double>(s.cell_cdf, g.ncells, (double)pk.rng.next());
+        pk.r.i = (int)(c % g.n1);
+        pk.r.j = (int)((c / g.n1) % g.n2);
+        pk.r.k = (int)(c / ((int64_t)g.n1 * g.n2));
+        pk.r.ci = (int32_t)c;
+        const float f0 = pk.rng.next(), f1 = pk.rng.next(), f2 = pk.rng.next();
+        if constexpr (G == GRID_CARTESIAN) {
+            const float x0 = __ldg(g.w1 + pk.r.i), y0 = __ldg(g.w2 + pk.r.j), z0 = __ldg(g.w3 + pk.r.k);
+            pk.r.p = make_float3(x0 + f0 * (__ldg(g.w1 + pk.r.i + 1) - x0), y0 + f1 * (__ldg(g.w2 + pk.r.j + 1) - y0),
+                                 z0 + f2 * (__ldg(g.w3 + pk.r.k + 1) - z0));
+        } else {
+            const double r0 = __ldg(g.rwd + pk.r.i), r1 = __ldg(g.rwd + pk.r.i + 1);
+            const double rad = cbrt(r0 * r0 * r0 + (double)f0 * (r1 * r1 * r1 - r0 * r0 * r0));
+            const double c0 = __ldg(g.cthd + pk.r.j), c1 = __ldg(g.cthd + pk.r.j + 1);
+            const double ct = c0 + (double)f1 * (c1 - c0);
+            const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            const float ph0 = __ldg(g.phw + pk.r.k);
+            const float ph = ph0 + f2 * (__ldg(g.phw + pk.r.k + 1) - ph0);
+            float sp, cp;
+            sincosf(ph, &sp, &cp);
+            pk.r.p = make_float3((float)(rad * st) * cp, (float)(rad * st) * sp, (float)(rad * ct));
+        }
+        const float u1 = pk.rng.next(), u2 = pk.rng.next();
+        set_dir(pk.r, isotropic_dir(u1, u2));
+        set_frequency(pk, d, o, sample_table(s.spec_nu, s.spec_cdf + (int64_t)src * s.nspec, s.nspec, pk.rng.next()));
+        pk.last_origin = pk.r.p;
+        if (a.peel && inline_peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
+    }
+    return true;
+}
+
+// Interaction at the packet's position (Sect. 2.2): absorbed when zeta > albedo, then
+// re-emitted isotropically with a frequency from the cell's emissivity row; otherwise scattered.
+// Returns false when the packet ends (terminate-on-absorb test mode).
+template <int G>
+__device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, const DevObs& o, const RunArgs& a,
+                                         const Tallies& t, double* sed_s, Packet& pk, LocalCounters& lc) {
+    lc.v[C_INTERACTIONS]++;
+    const float z = pk.rng.next();
+    if (z > pk.dust.albedo) {
+        lc.v[C_ABSORB]++;
+        if (a.terminate_on_absorb) {
+            lc.v[C_ABSORBED_TERM]++;
+            return false;
+        }
+        const float u1 = pk.rng.next(), u2 = pk.rng.next();
+        set_dir(pk.r, isotropic_dir(u1, u2));
+        const int row = __ldg(d.emit_row + pk.r.ci);
+        set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
+        if (a.peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
+    } else {
+        lc.v[C_SCATTER]++;
+        const float mu = hg_mu(d.g, pk.rng.next());
+        const float u2 = pk.rng.next();
+        const float3 uin = pk.r.u;
+        set_dir(pk.r, scatter_dir(uin, mu, u2));
+        if (a.peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, uin, PEEL_HG, false, pk.dust.chi, pk.sbin, lc);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tally_escape(const DevObs& o, const Tallies& t, const Packet& pk, unsigned* esc_s) {
+    if (pk.sbin < 0) return;
+    int bm = (int)floorf((pk.r.u.z + 1.f) * 0.5f * N_ESC_MU);
+    bm = bm < 0 ? 0 : (bm >= N_ESC_MU ? N_ESC_MU - 1 : bm);
+    if (esc_s) atomicAdd(esc_s + bm * o.nsed + pk.sbin, 1u);
+    else atomicAdd(t.esc + (int64_t)bm * o.nsed + pk.sbin, 1ull);
+}
+
+}  // namespace hrt

@@ -1,0 +1,60 @@
+"""Shared helpers of the GPU tests (seeded inputs, oracle models, library models)."""
+import math
+
+import numpy as np
+
+from oracle import mc as M
+from paper_1112_1071_gb300 import workloads as W
+
+
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch
+
+
+def dev(a, dtype=None):
+    torch = torch_cuda()
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda().contiguous()
+
+
+def spherical_test_grid(hole=True, nphi=4):
+    rw = np.array([0.3, 0.5, 0.9, 1.4, 2.0]) * W.AU if hole else np.array([0.0, 0.5, 0.9, 1.4, 2.0]) * W.AU
+    tw = np.array([0.0, 0.4, 1.1, math.pi / 2, 2.2, math.pi])
+    pw = np.array([0.0, 1.0, 2.5, 4.0, 2 * math.pi]) if nphi == 4 else np.array([0.0, 2 * math.pi])
+    return [rw, tw, pw]
+
+
+def workload_from_walls(grid_type, walls, rho=None, seed=21):
+    shape = tuple(len(w) - 1 for w in walls)
+    if rho is None:
+        rng = np.random.default_rng(seed)
+        rho = rng.uniform(0.5, 2.0, shape[::-1]).astype(np.float32) * 1e-18
+    nu, chi, alb, g = W.dust_table()
+    return W.Workload(name="walls", grid_type=grid_type, walls=[np.asarray(w, float) for w in walls], rho=rho,
+                      nu=nu, chi=chi, albedo=alb, g=g, T_nodes=W.temperature_nodes(),
+                      sources=[dict(pos=(0.0, 0.0, 0.0), L=W.LSUN, Teff=5800.0)],
+                      obs_incl=np.radians([30.0]), obs_az=np.zeros(1), seed=seed)
+
+
+def random_points_in_grid(om, n, rng, radius):
+    """Points strictly inside the grid with their cells located by the oracle."""
+    pts, dirs, cells = [], [], []
+    out = np.zeros(3)
+    c = np.zeros(3, np.int32)
+    while len(pts) < n:
+        p = rng.uniform(-radius, radius, 3)
+        if om.gtype == 1 and np.linalg.norm(p) >= radius:
+            continue
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        st = M.lib().or_locate(om._struct, M._ptr(p), M._ptr(u), M._ptr(out), M._ptr(c, M._ip))
+        if st != 0 or not np.allclose(out, p):
+            continue        # skip points in the hole (the locate moved them)
+        pts.append(p.copy())
+        dirs.append(u)
+        cells.append(c.copy())
+    return np.array(pts), np.array(dirs), np.array(cells, np.int32)
