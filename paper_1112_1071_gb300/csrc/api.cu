@@ -102,7 +102,7 @@ struct hrt_ctx {
     DBuf<int32_t> d_abort;
     DBuf<unsigned long long> d_work;
     unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // start, after propagation, end, before propagation
     double Q_prev = std::numeric_limits<double>::infinity();
     bool have_Q = false;
     double L_tot = 0.0;
@@ -723,6 +723,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     }
     CK(launch_stamp(ctx->d_work.p + 1, s), "stamp");
     launched++;
+    CK(cudaEventRecord(ctx->ev[3], s), "event");
     cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
                                                  : launch_propagate_event(job, L, s, &launched);
     CK(e, "propagate");
@@ -774,7 +775,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     st.n_peel_crossings = (int64_t)h[C_PEEL_CROSSINGS];
     st.n_killed = (int64_t)h[C_KILLED];
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[1]);
     st.ms_propagate = ms;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
     st.ms_total = ms;

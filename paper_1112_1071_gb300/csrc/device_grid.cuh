@@ -144,8 +144,11 @@ __device__ __forceinline__ R cone_root(R px, R py, R pz, R ux, R uy, R uz, R cw,
 // only while moving inwards.
 template <typename R>
 __device__ __forceinline__ R sphere_out(R rr, R b, R rw2) {
-    const R disc = b * b - (rr - rw2);
-    const R s = -b + sqrt(disc > R(0) ? disc : R(0));
+    const R c = rr - rw2;
+    const R disc = b * b - c;
+    const R sq = sqrt(disc > R(0) ? disc : R(0));
+    // far root without cancellation: -c / (b + sq) when moving outwards, -b + sq otherwise
+    const R s = b > R(0) ? -c / (b + sq) : -b + sq;
     return s > R(0) ? s : R(0);
 }
 template <typename R>
