@@ -173,6 +173,12 @@ int hrt_get_temperature_device(hrt_ctx* ctx, double* d_out, int64_t n);
 int hrt_get_sed_device(hrt_ctx* ctx, double* d_out, int64_t n);
 int64_t hrt_num_cells(const hrt_ctx* ctx);
 
+/* After an HRT_ETIMEDOUT: the state of up to 32 packets the watchdog stopped, 16 floats each
+ * (lane mode, packet id, interactions, optical depth, position[3] and direction[3] in the
+ * scaled unit, cell index[3], frequency, peel observer, step or round count).  `out` must hold
+ * 512 floats.  Returns the number of records (>= 0) or a negative hrt_status. */
+int hrt_get_watchdog_report(hrt_ctx* ctx, float* out, int64_t n);
+
 /* Warm start / resume: replace the temperatures (K, > 0) used by the next iteration. */
 int hrt_set_temperature(hrt_ctx* ctx, const double* T, int64_t n);
 int hrt_set_temperature_device(hrt_ctx* ctx, const double* d_T, int64_t n);

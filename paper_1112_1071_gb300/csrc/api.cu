@@ -101,6 +101,8 @@ struct hrt_ctx {
     DBuf<unsigned int> d_hist;
     DBuf<int32_t> d_abort;
     DBuf<unsigned long long> d_work;
+    DBuf<float> d_report;
+    DBuf<unsigned> d_report_count;
     unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // start, after propagation, end, before propagation
     double Q_prev = std::numeric_limits<double>::infinity();
@@ -409,6 +411,8 @@ int prepare(hrt_ctx* ctx) {
     CK(ctx->d_hist.alloc(256), "select histogram");
     CK(ctx->d_abort.alloc(1), "abort flag");
     CK(ctx->d_work.alloc(2), "work counter");
+    CK(ctx->d_report.alloc(WD_REPORTS * WD_FIELDS), "watchdog report");
+    CK(ctx->d_report_count.alloc(1), "watchdog report");
     if (!ctx->h_stats) CK(cudaMallocHost(&ctx->h_stats, sizeof(unsigned long long) * (N_COUNTERS + 8)), "pinned stats");
     for (auto& e : ctx->ev)
         if (!e) CK(cudaEventCreate(&e), "event");
@@ -681,6 +685,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     CK(cudaMemsetAsync(ctx->d_counters.p, 0, ctx->d_counters.n * sizeof(unsigned long long), s), "zero counters");
     CK(cudaMemsetAsync(ctx->d_abort.p, 0, sizeof(int32_t), s), "zero abort");
     CK(cudaMemsetAsync(ctx->d_work.p, 0, ctx->d_work.n * sizeof(unsigned long long), s), "zero work");
+    CK(cudaMemsetAsync(ctx->d_report_count.p, 0, sizeof(unsigned), s), "zero report");
 
     PropagateJob job;
     job.grid = ctx->grid;
@@ -694,6 +699,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     job.tal.esc = ctx->d_esc.p;
     job.tal.counters = ctx->d_counters.p;
     job.tal.abort_flag = ctx->d_abort.p;
+    job.tal.report = ctx->d_report.p;
+    job.tal.report_count = ctx->d_report_count.p;
     RunArgs& A = job.args;
     A = RunArgs{};
     A.n_packets = n_packets;
@@ -897,6 +904,19 @@ int hrt_set_temperature_device(hrt_ctx* ctx, const double* d_T, int64_t n) {
     CK(cudaMemcpyAsync(ctx->d_T.p, d_T, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "copy T");
     ctx->have_T = true;
     return HRT_OK;
+}
+
+int hrt_get_watchdog_report(hrt_ctx* ctx, float* out, int64_t n) {
+    if (!ctx || !out) return HRT_EINVAL;
+    if (n < (int64_t)WD_REPORTS * WD_FIELDS) return ctx->fail(HRT_EINVAL, "report needs %d floats", WD_REPORTS * WD_FIELDS);
+    if (!ctx->d_report.p) return 0;
+    DeviceGuard dg(ctx->device);
+    unsigned cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, ctx->d_report_count.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream), "report");
+    CK(cudaMemcpyAsync(out, ctx->d_report.p, sizeof(float) * WD_REPORTS * WD_FIELDS, cudaMemcpyDeviceToHost, ctx->stream),
+       "report");
+    CK(cudaStreamSynchronize(ctx->stream), "report");
+    return (int)(cnt < (unsigned)WD_REPORTS ? cnt : (unsigned)WD_REPORTS);
 }
 
 int hrt_set_iteration(hrt_ctx* ctx, int iteration) {

@@ -28,7 +28,7 @@ struct Ray {
     int32_t ci;          // linear cell index (k n2 + j) n1 + i
 };
 
-enum WalkEvent : int32_t { EV_INTERACT = 0, EV_ESCAPE = 1, EV_ABORT = 2 };
+enum WalkEvent : int32_t { EV_INTERACT = 0, EV_ESCAPE = 1, EV_ABORT = 2, EV_STUCK = 3 };
 
 __device__ __forceinline__ void set_dir(Ray& r, float3 u) {
     r.u = u;
@@ -178,6 +178,10 @@ __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& a
     const float tol = 2e-6f * sqrtf(rr) + 1e-30f;
     float best;
     const float rout = __ldg(g.rw + r.i + 1);
+    // A ray enters the inner sphere only when clearly moving inwards: a ray tangent to the
+    // sphere touches it at one point, and FP32 rounding of p.u around zero must not make it
+    // cross back and forth there.
+    const float b_in = -1e-6f * sqrtf(rr);
     if (rout < g.r_fp64) {
         const double pd[3] = {r.p.x, r.p.y, r.p.z}, ud[3] = {r.u.x, r.u.y, r.u.z};
         const double rrd = pd[0] * pd[0] + pd[1] * pd[1] + pd[2] * pd[2];
@@ -185,14 +189,14 @@ __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& a
         const double ro = __ldg(g.rwd + r.i + 1), ri = __ldg(g.rwd + r.i);
         best = (float)sphere_out<double>(rrd, bd, ro * ro);
         axis = 0; dir = 1;
-        if (ri > 0.0 && bd < 0.0) {
+        if (ri > 0.0 && bd < (double)b_in) {
             const float s = (float)sphere_in<double>(rrd, bd, ri * ri);
             if (s < best) { best = s; dir = -1; }
         }
     } else {
         best = sphere_out<float>(rr, b, __ldg(g.r2w + r.i + 1));
         axis = 0; dir = 1;
-        if (b < 0.f && __ldg(g.rw + r.i) > 0.f) {
+        if (b < b_in && __ldg(g.rw + r.i) > 0.f) {
             const float s = sphere_in<float>(rr, b, __ldg(g.r2w + r.i));
             if (s < best) { best = s; dir = -1; }
         }
@@ -359,9 +363,14 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Zero-length crossings in a row beyond which the ray is moved on by a hair: a ray grazing
-// a curved wall within rounding could otherwise cross it back and forth without advancing.
+// Near-zero crossings (shorter than 1e-6 of the radius) in a row beyond which the ray is
+// moved on by a hair: a ray grazing a curved wall within rounding could otherwise cross it back
+// and forth without advancing.  A ray that still makes no headway after MAX_WALK_STEPS
+// crossings is ended and counted (C_STUCK); the walk therefore always terminates.
 constexpr int ZERO_RUN_LIMIT = 16;
+constexpr unsigned MAX_WALK_STEPS = 1u << 22;
+
+__device__ __forceinline__ bool tiny_step(const Ray& r, float l) { return l <= 1e-6f * sqrtf(dot3(r.p, r.p)); }
 
 __device__ __forceinline__ void nudge(Ray& r) {
     const float h = 1e-6f * fmaxf(sqrtf(dot3(r.p, r.p)), 1e-6f);
@@ -376,7 +385,7 @@ __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi,
                                              float tau_stop) {
     float tau = 0.f;
     int zero_run = 0;
-    for (;;) {
+    for (unsigned steps = 0; steps < MAX_WALK_STEPS; ++steps) {
         int axis, dir;
         const float l = cell_exit<G>(g, r, axis, dir);
         tau += __ldg(g.rhoL + r.ci) * chi * l;
@@ -384,10 +393,11 @@ __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi,
         if (tau > tau_stop) return tau;
         if (cell_step<G>(g, r, l, axis, dir)) return tau;
         if constexpr (G == GRID_SPHERICAL) {
-            if (l == 0.f && ++zero_run > ZERO_RUN_LIMIT) { nudge(r); zero_run = 0; }
-            else if (l != 0.f) zero_run = 0;
+            if (!tiny_step(r, l)) zero_run = 0;
+            else if (++zero_run > ZERO_RUN_LIMIT) { nudge(r); zero_run = 0; }
         }
     }
+    return tau;
 }
 
 }  // namespace hrt

@@ -82,7 +82,12 @@ struct Tallies {
     unsigned long long* esc;       // [10][nsed] escaping packet counts (x eps = energy)
     unsigned long long* counters;  // [N_COUNTERS]
     int32_t* abort_flag;           // set by the watchdog
+    float* report;                 // [WD_REPORTS][WD_FIELDS] state of lanes stopped by the watchdog
+    unsigned* report_count;
 };
+
+constexpr int WD_REPORTS = 32;
+constexpr int WD_FIELDS = 16;
 
 enum Counter {
     C_ESCAPED = 0,
@@ -95,6 +100,7 @@ enum Counter {
     C_PEEL_CROSSINGS,
     C_PACKETS_DONE,
     C_WATCHDOG,
+    C_STUCK,          // rays ended after MAX_WALK_STEPS crossings without reaching an event
     N_COUNTERS
 };
 

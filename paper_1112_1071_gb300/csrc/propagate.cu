@@ -76,8 +76,12 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
         int axis, dir;
         const float l = cell_exit<G>(g, pk.r, axis, dir);
         if constexpr (G == GRID_SPHERICAL) {
-            if (l == 0.f && ++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
-            else if (l != 0.f) zero_run = 0;
+            if (!tiny_step(pk.r, l)) zero_run = 0;
+            else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
+        }
+        if (check >= MAX_WALK_STEPS) {
+            lc.v[C_STUCK]++;
+            return EV_STUCK;
         }
         const float rho = __ldg(g.rhoL + pk.r.ci);
         const float k = rho * chi;
@@ -127,6 +131,10 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
                 lc.v[C_WATCHDOG]++;
                 break;
             }
+            if (ev == EV_STUCK) {
+                lc.v[C_KILLED]++;
+                break;
+            }
             if (++pk.nint > a.max_interactions) {
                 lc.v[C_KILLED]++;
                 break;
@@ -173,7 +181,7 @@ cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cud
 }
 
 // ---------------------------------------------------------------- event kernel
-enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_DONE };
+enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE };
 
 // Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
 // With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
@@ -216,6 +224,7 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
     int32_t dep_ci = -1;
     double dep_val = 0.0, dep_rate = 0.0;
     int zero_run = 0;
+    unsigned ray_steps = 0;    // crossings of the current ray since it started or last interacted
     bool aborted = false;
 
     // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction)
@@ -224,6 +233,8 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
         pk.r.p = porg;
         set_dir(pk.r, make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2)));
         tau = 0.f;
+        ray_steps = 0;
+        zero_run = 0;
         mode = M_PEEL;
         if (prelocate && !grid_locate<G>(g, pk.r)) mode = M_PEEL_DONE;
     };
@@ -238,8 +249,33 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
         } else {
             tau = -logf(pk.rng.next());
             dep_rate = a.epsL0 * (double)pk.dust.kappa;
+            ray_steps = 0;
+            zero_run = 0;
             mode = M_WALK;
         }
+    };
+    // Watchdog (warp-uniform call): past the time budget, every live lane stops, records its
+    // state in the report buffer (first WD_REPORTS lanes) and is counted; nothing traps.
+    unsigned rounds = 0;
+    auto watchdog = [&](unsigned where) {
+        bool ab = false;
+        if (lane == 0) ab = past_deadline(a, t);
+        if (!__shfl_sync(FULL, ab ? 1 : 0, 0)) return;
+        aborted = true;
+        if (mode == M_DONE) return;
+        lc.v[C_WATCHDOG]++;
+        const unsigned slot = atomicAdd(t.report_count, 1u);
+        if (slot < (unsigned)WD_REPORTS) {
+            float* r = t.report + slot * WD_FIELDS;
+            r[0] = (float)mode; r[1] = (float)pk.rng.pkt; r[2] = (float)pk.nint; r[3] = tau;
+            r[4] = pk.r.p.x; r[5] = pk.r.p.y; r[6] = pk.r.p.z;
+            r[7] = pk.r.u.x; r[8] = pk.r.u.y; r[9] = pk.r.u.z;
+            r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
+            r[13] = pk.nu; r[14] = (float)pobs; r[15] = (float)where;
+        }
+        if (dep_ci >= 0 && dep_val != 0.0) atomicAdd(t.acc + dep_ci, dep_val);
+        dep_ci = -1;
+        mode = M_DONE;
     };
     auto end_packet = [&]() {
         if (dep_ci >= 0 && dep_val != 0.0) atomicAdd(t.acc + dep_ci, dep_val);
@@ -251,7 +287,9 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
 
     for (;;) {
         // ------------------------------------------------------------ event phase
-        if (mode == M_ESCAPED) {
+        if (mode == M_KILLED) {
+            end_packet();
+        } else if (mode == M_ESCAPED) {
             lc.v[C_ESCAPED]++;
             tally_escape(o, t, pk, st.esc);
             end_packet();
@@ -307,6 +345,8 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
                 pk.r = saved;
                 tau = -logf(pk.rng.next());
                 dep_rate = a.epsL0 * (double)pk.dust.kappa;
+                ray_steps = 0;
+                zero_run = 0;
                 mode = M_WALK;
             }
         }
@@ -334,7 +374,7 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
                 }
             }
         }
-        const unsigned live = __ballot_sync(FULL, mode != M_DONE);
+        unsigned live = __ballot_sync(FULL, mode != M_DONE);
         if (live == 0) break;
         // ------------------------------------------------------------ walk phase
         const int thr = min(a.regroup, __popc(live));
@@ -387,26 +427,27 @@ __global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSourc
                 if (!stop) {
                     if (cell_step<G>(g, pk.r, l, axis, dir)) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
                     if constexpr (G == GRID_SPHERICAL) {
-                        if (l == 0.f && ++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
-                        else if (l != 0.f) zero_run = 0;
+                        if (!tiny_step(pk.r, l)) zero_run = 0;
+                        else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
                     }
+                    if (++ray_steps > MAX_WALK_STEPS && (mode == M_WALK || mode == M_PEEL)) {
+                        lc.v[C_STUCK]++;
+                        if (mode == M_WALK) {
+                            lc.v[C_KILLED]++;
+                            mode = M_KILLED;
+                        } else {
+                            tau = F_INF;           // the peel ray is dropped (zero weight)
+                            mode = M_PEEL_DONE;
+                        }
+                    }
+                } else {
+                    ray_steps = 0;
                 }
             }
             flush_deposit<WAGG>(t.acc, flushing, fci, fval);
-            if (((++steps) & 4095u) == 0) {
-                bool ab = false;
-                if (lane == 0) ab = past_deadline(a, t);
-                if (__shfl_sync(FULL, ab ? 1 : 0, 0)) {
-                    aborted = true;
-                    if (mode != M_DONE) {
-                        lc.v[C_WATCHDOG]++;
-                        if (dep_ci >= 0 && dep_val != 0.0) atomicAdd(t.acc + dep_ci, dep_val);
-                        dep_ci = -1;
-                        mode = M_DONE;
-                    }
-                }
-            }
+            if (((++steps) & 4095u) == 0) watchdog(steps);
         }
+        if (((++rounds) & 255u) == 0) watchdog(rounds);
     }
     if (dep_ci >= 0 && dep_val != 0.0) atomicAdd(t.acc + dep_ci, dep_val);
     flush_counters(lc, t.counters);

@@ -91,6 +91,7 @@ _SIGS = {
     "hrt_num_cells": (C.c_int64, [_vp]),
     "hrt_set_temperature": (C.c_int, [_vp, _vp, _i64]),
     "hrt_set_temperature_device": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_get_watchdog_report": (C.c_int, [_vp, _vp, _i64]),
     "hrt_set_iteration": (C.c_int, [_vp, C.c_int]),
     "hrt_set_model_id": (C.c_int, [_vp, C.c_uint32]),
     "hrt_step_philox": (C.c_int, [_i64, _vp, _vp, _vp, _vp]),

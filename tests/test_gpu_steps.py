@@ -185,3 +185,38 @@ def test_tables_and_temperature_inversion_fp64():
     m.step("hrt_step_temperature", len(A), Ad.data_ptr(), out.data_ptr())
     want, _, _ = T.temperature_from_adot(A, om.T_nodes, om.dust.E)
     np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-12)
+
+
+def test_ray_tangent_to_a_sphere_wall_terminates():
+    # a peel ray from a point on the sphere r_15 of the disk grid, exactly perpendicular to the
+    # radius there: in FP32 it must not cross the wall back and forth
+    torch = torch_cuda()
+    wl = W.flared_disk()
+    L0 = wl.walls[0][-1]
+    r15 = wl.walls[0][15] / L0
+    u = np.array([0.526783, 0.0, 0.85])
+    u /= np.linalg.norm(u)
+    v = np.array([-u[2], 0.0, u[0]])                   # perpendicular to u in the x-z plane
+    q = np.array([0.0, 1.0, 0.0])
+    rng = np.random.default_rng(6)
+    pts, dirs = [], []
+    for k in range(256):
+        a = rng.uniform(0, 2 * np.pi)
+        rad = np.cos(a) * v + np.sin(a) * q                # radius direction perpendicular to u
+        pts.append(rad * r15 * L0)
+        dirs.append(u)
+    p = np.array(pts).astype(np.float32)
+    d = np.array(dirs).astype(np.float32)
+    om = M.OracleModel(wl)
+    om.struct(np.zeros(om.nc, np.int32))
+    m = hrt.Model(wl)
+    nus = np.full(len(p), 3e14, np.float32)
+    tau = torch.empty(len(p), dtype=torch.float32, device="cuda")
+    pd, ud, nd = dev(p), dev(d), dev(nus)
+    m.step("hrt_step_tau_to_edge", len(p), pd.data_ptr(), ud.data_ptr(), nd.data_ptr(), tau.data_ptr())
+    got = tau.cpu().numpy()
+    chi, _ = _oracle_dust(om, 3e14)
+    want = np.array([M.lib().or_tau_to_edge(om._struct, M._ptr(p[k].astype(np.float64)),
+                                            M._ptr(d[k].astype(np.float64)), chi) for k in range(len(p))])
+    assert np.all(np.isfinite(got))
+    np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-6)
