@@ -220,6 +220,30 @@ int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* 
 /* Tabulated E(T) [nT] and emissivity cdf [nT][nnu] as built on the device (copied to host). */
 int hrt_get_tables(hrt_ctx* ctx, double* E, int64_t nE, float* cdf, int64_t ncdf);
 
+/* ------------------------------------------------------------------ allocation-free quantile
+ * The paper has no counterpart: this is a convenience for callers of the library that cannot
+ * allocate device memory, such as a host framework whose allocator already owns the device's
+ * memory, or latency-bound code that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree can impose.  It computes the same statistic as the Q of
+ * hrt_run_iteration: the nearest-rank p-quantile of max(prev/cur, cur/prev) over the cells
+ * whose density rho is > 0, written as one double to d_out (NaN when no cell holds dust).
+ * d_prev, d_cur (n doubles), d_rho (n floats) and d_out are caller-owned device pointers;
+ * the work is ordered on `stream` (cudaStream_t as void*) and the call does not wait for it.
+ *
+ * It allocates nothing: its only scratch is a fixed 1,056-byte array in the library's static
+ * device memory, held by every GPU that loads the library until the process exits.  The first call on
+ * a device looks up that array's device address (with that device current), so make the first
+ * call on each device before any stream capture.  Every call on a device uses the same array
+ * and clears it at its start: calls that overlap on the GPU (different streams, or host
+ * threads) race and give wrong results; serialise them.
+ *
+ * Limit: 1 <= n <= HRT_NOALLOC_MAX_CELLS (2^31 - 1, the range of its 32-bit bin counts).
+ * Returns HRT_OK, HRT_EINVAL (n out of range, a null pointer, p outside (0, 1]) or HRT_ECUDA;
+ * it has no context, so hrt_last_error() does not describe its failures. */
+#define HRT_NOALLOC_MAX_CELLS 2147483647LL
+int hrt_quantile_ratio_noalloc(int64_t n, const double* d_prev, const double* d_cur, const float* d_rho,
+                               double p, double* d_out, void* stream);
+
 /* ------------------------------------------------------------------ batched models (Sect. 3 analogue)
  * Many contexts on the same device run each Lucy iteration in one persistent launch whose
  * blocks pull (model, packet chunk) work items from a device queue (largest first), the

@@ -102,6 +102,7 @@ _SIGS = {
     "hrt_step_sample_source": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
     "hrt_step_temperature": (C.c_int, [_vp, _i64, _vp, _vp]),
     "hrt_get_tables": (C.c_int, [_vp, _vp, _i64, _vp, _i64]),
+    "hrt_quantile_ratio_noalloc": (C.c_int, [_i64, _vp, _vp, _vp, C.c_double, _vp, _vp]),
     "hrt_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int]),
     "hrt_batch_destroy": (C.c_int, [_vp]),
     "hrt_batch_run": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(hrt_run_params), _vp, C.POINTER(C.c_int)]),
