@@ -18,125 +18,8 @@
 
 using namespace hrt;
 
-namespace {
+#include "ctx_internal.h"
 
-constexpr double PI = 3.14159265358979323846;
-constexpr double C_LIGHT_CGS = 2.99792458e10;
-constexpr int NSPEC = 1000;            // source spectrum nodes over the dust band
-constexpr int DEFAULT_NSED = 250;
-
-template <class T>
-struct DBuf {
-    T* p = nullptr;
-    size_t n = 0;
-    cudaError_t alloc(size_t count) {
-        if (count == n && p) return cudaSuccess;
-        release();
-        if (count == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-        if (e != cudaSuccess) { p = nullptr; return e; }
-        n = count;
-        return cudaSuccess;
-    }
-    cudaError_t upload(const T* h, size_t count, cudaStream_t s) {
-        cudaError_t e = alloc(count);
-        if (e != cudaSuccess || count == 0) return e;
-        return cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s);
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-    }
-};
-
-struct PointSrc {
-    double x[3];
-    double L;
-    double teff;
-    std::vector<double> unu, uf;
-};
-
-}  // namespace
-
-struct hrt_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    uint64_t seed = 0;
-    uint32_t model_id = 0;
-    int iteration = 0;
-    std::string err;
-
-    // ---- problem (host copies)
-    int gtype = -1;
-    int n[3] = {0, 0, 0};
-    std::vector<double> w[3];
-    double L0 = 1.0;
-    std::vector<float> rho;
-    int64_t n_dust = 0;
-    std::vector<double> nu, chi, alb, Tn;
-    double g = 0.0;
-    std::vector<PointSrc> pts;
-    std::vector<double> Lcell;
-    double cell_teff = 0.0;
-    int nobs = 0, nsed = DEFAULT_NSED, img_nx = 0, img_ny = 0, nimg = 0;
-    double lam_min_um = 0.1, lam_max_um = 1000.0, img_half = 0.0;
-    std::vector<double> incl, az, img_lam;
-    bool dirty_grid = true, dirty_dust = true, dirty_src = true, dirty_obs = true, have_T = false;
-
-    // ---- device problem
-    DBuf<float> d_rhoL, d_w1, d_w2, d_w3, d_rw, d_r2w, d_thw, d_cth, d_sth, d_phw, d_cph, d_sph;
-    DBuf<double> d_rwd, d_cthd, d_sthd, d_va, d_vb, d_vc;
-    DBuf<float> d_lnu, d_inv_dlnu, d_lchi, d_alb, d_nuf, d_cdf_emit;
-    DBuf<double> d_nu, d_kappa, d_Tn, d_lnT, d_E, d_lnE;
-    DBuf<float> d_src_pos, d_spec_nu, d_spec_cdf;
-    DBuf<double> d_src_cdf, d_cell_cdf, d_spec_nud, d_teff, d_unu, d_uf;
-    DBuf<int> d_uoff, d_un;
-    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey;
-    DBuf<int32_t> d_img_bin;
-    // ---- device state
-    DBuf<double> d_T, d_adot, d_acc, d_sed, d_img;
-    DBuf<int32_t> d_row;
-    DBuf<unsigned long long> d_keys, d_esc, d_counters, d_state;
-    DBuf<unsigned int> d_hist;
-    DBuf<int32_t> d_abort;
-    DBuf<unsigned long long> d_work;
-    DBuf<float> d_report;
-    DBuf<unsigned> d_report_count;
-    unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // start, after propagation, end, before propagation
-    double Q_prev = std::numeric_limits<double>::infinity();
-    bool have_Q = false;
-    double L_tot = 0.0;
-    double last_eps = 0.0;
-
-    DevGrid grid{};
-    DevDust dust{};
-    DevSources src{};
-    DevObs obs{};
-
-    int fail(int code, const char* fmt, ...) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof(buf), fmt, ap);
-        va_end(ap);
-        err = buf;
-        return code;
-    }
-    int cuda(cudaError_t e, const char* what) {
-        if (e == cudaSuccess) return HRT_OK;
-        cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? HRT_ENOMEM : HRT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-    }
-    int64_t ncells() const { return (int64_t)n[0] * n[1] * n[2]; }
-};
-
-#define CK(call, what)                                   \
-    do {                                                 \
-        int _rc = ctx->cuda((call), what);               \
-        if (_rc != HRT_OK) return _rc;                   \
-    } while (0)
 
 namespace {
 
@@ -229,8 +112,9 @@ int stage_grid(hrt_ctx* ctx) {
         g.thw = ctx->d_thw.p; g.cth = ctx->d_cth.p; g.sth = ctx->d_sth.p; g.cthd = ctx->d_cthd.p; g.sthd = ctx->d_sthd.p;
         g.phw = ctx->d_phw.p; g.cph = ctx->d_cph.p; g.sph = ctx->d_sph.p;
         g.r0 = rw[0];
-        // FP64 sphere solves within four inner radii (or the first shell without a hole)
-        g.r_fp64 = (float)(4.0 * (rwd[0] > 0 ? rwd[0] : rwd[1]));
+        // FP64 sphere solves for the shells within 25% of the inner radius (or of the first
+        // wall without a hole); elsewhere the stable root forms are accurate in FP32
+        g.r_fp64 = (float)(1.25 * (rwd[0] > 0 ? rwd[0] : rwd[1]));
         g.sin_fp64 = 0.1f;
         for (int i = 0; i < nr; ++i) va[i] = (std::pow(ctx->w[0][i + 1], 3) - std::pow(ctx->w[0][i], 3)) / 3.0;
         for (int j = 0; j < nt; ++j) vb[j] = std::cos(ctx->w[1][j]) - std::cos(ctx->w[1][j + 1]);
@@ -420,6 +304,11 @@ int prepare(hrt_ctx* ctx) {
 }
 
 }  // namespace
+
+int hrt::prepare_ctx(hrt_ctx* ctx) {
+    DeviceGuard dg(ctx->device);
+    return prepare(ctx);
+}
 
 // ==================================================================== ABI
 extern "C" {
@@ -672,11 +561,11 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     const int64_t nc = ctx->ncells();
     int launched = 0;
     CK(cudaEventRecord(ctx->ev[0], s), "event");
-    if (P.update_temperature) {
-        CK(cudaMemsetAsync(ctx->d_acc.p, 0, nc * sizeof(double), s), "zero acc");
-        CK(launch_emit_rows(ctx->d_T.p, ctx->d_row.p, nc, ctx->d_lnT.p, (int)ctx->Tn.size(), s), "emission rows");
-        launched++;
-    }
+    if (P.update_temperature) CK(cudaMemsetAsync(ctx->d_acc.p, 0, nc * sizeof(double), s), "zero acc");
+    // re-emission rows from the temperatures this pass uses (every pass: the temperatures may
+    // have been set since the last update)
+    CK(launch_emit_rows(ctx->d_T.p, ctx->d_row.p, nc, ctx->d_lnT.p, (int)ctx->Tn.size(), s), "emission rows");
+    launched++;
     if (P.peel) {
         CK(cudaMemsetAsync(ctx->d_sed.p, 0, ctx->d_sed.n * sizeof(double), s), "zero sed");
         CK(cudaMemsetAsync(ctx->d_img.p, 0, ctx->d_img.n * sizeof(double), s), "zero image");
@@ -743,6 +632,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         tj.ncells = nc;
         tj.rhoL = ctx->d_rhoL.p;
         tj.acc = ctx->d_acc.p;
+        tj.acc_scale = A.epsL0;
+        ctx->acc_scale = A.epsL0;
         tj.va = ctx->d_va.p; tj.vb = ctx->d_vb.p; tj.vc = ctx->d_vc.p;
         tj.E = ctx->d_E.p; tj.lnE = ctx->d_lnE.p; tj.lnT = ctx->d_lnT.p; tj.Tn = ctx->d_Tn.p;
         tj.nT = (int)ctx->Tn.size();
@@ -842,7 +733,10 @@ int hrt_get_specific_energy(hrt_ctx* ctx, double* out, int64_t n) {
 int hrt_get_absorbed(hrt_ctx* ctx, double* out, int64_t n) {
     if (!ctx) return HRT_EINVAL;
     if (n < ctx->ncells()) return ctx->fail(HRT_EINVAL, "output shorter than the cell count");
-    return get_dev(ctx, ctx->d_acc.p, ctx->d_acc.n * 8, out, ctx->ncells() * 8, true);
+    const int rc = get_dev(ctx, ctx->d_acc.p, ctx->d_acc.n * 8, out, ctx->ncells() * 8, true);
+    if (rc != HRT_OK) return rc;
+    for (int64_t c = 0; c < ctx->ncells(); ++c) out[c] *= ctx->acc_scale;   // sum eps kappa l in cgs
+    return HRT_OK;
 }
 int hrt_get_sed(hrt_ctx* ctx, double* out, int64_t n) {
     if (!ctx) return HRT_EINVAL;

@@ -1,0 +1,373 @@
+// Event-based persistent propagation (Sect. 2.2, Eq. 2, Sect. 2.6.2).
+//
+// Every lane of a persistent warp runs a small state machine: it takes a packet, emits it,
+// walks it to its next event (interaction or escape), handles the event (scatter, or absorb
+// and re-emit), walks its peel-off rays, and takes the next packet when the history ends.
+// A round has two phases:
+//   * event phase: lanes with a finished walk handle their event (short, divergent code);
+//   * walk phase: all walking lanes (packet rays and peel rays share one step) take cell
+//     crossings together while at least `regroup` lanes are walking, so the walk -- where
+//     nearly all time goes -- runs in long converged loops.
+// Lanes that need a packet draw consecutive packet ids with one atomic per warp.  Packet p
+// always draws from its own Philox stream, so the histories do not depend on which lane or
+// launch shape runs them.  Deposits are the FP32 products kappa * l (scaled length), merged
+// in registers while the packet stays in one cell; at each step, lanes of a warp that flush
+// into the same cell add one FP64 atomic.  The FP64 accumulators therefore hold sum kappa l,
+// and the temperature update multiplies by eps L0 (Eq. 2) in FP64.
+//
+// The same loop serves the batched launch: warps pull (model, packet range) chunks of many
+// models from one queue (largest models first) -- the device-side form of the paper's chunked
+// packet scheduling (Sect. 3).
+#include "propagate_common.cuh"
+
+namespace hrt {
+
+enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE };
+
+// Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
+// With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
+// group adds its sum with one FP64 atomic.
+template <bool WAGG>
+__device__ __forceinline__ void flush_deposit(double* acc, bool flushing, int32_t ci, float v) {
+    if constexpr (WAGG) {
+        const unsigned lane = threadIdx.x & 31u;
+        const int key = flushing ? ci : -1 - (int)lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (!flushing) return;
+        if (__popc(peers) == 1) {
+            atomicAdd(acc + ci, (double)v);
+            return;
+        }
+        float sum = 0.f;
+        for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
+        if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(acc + ci, (double)sum);
+    } else {
+        if (flushing) atomicAdd(acc + ci, (double)v);
+    }
+}
+
+// The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
+// `need` (ballot) lanes want a packet and returns this lane's packet id, or -1 when none is left.
+template <int G, bool WAGG, class Fetch>
+__device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, const DevSources& s, const DevObs& o,
+                                           const RunArgs& a, const Tallies& t, const SharedTallies& st,
+                                           LocalCounters& lc, Fetch&& fetch) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    Packet pk;                 // the packet; pk.r is the ray currently walked (packet or peel ray)
+    Ray saved;                 // packet ray while its peel rays are walked
+    float3 porg = make_float3(0.f, 0.f, 0.f);   // origin of the peel rays (event position)
+    float3 uin = make_float3(0.f, 0.f, 1.f);    // incoming direction at a scattering (HG peel)
+    float tau = 0.f;           // optical depth left (packet) or accumulated (peel ray)
+    int32_t mode = M_NEED;
+    int32_t pobs = 0, pkind = PEEL_ISO, prelocate = 0;
+    int32_t dep_ci = -1;
+    float dep_val = 0.f;       // kappa * l (scaled length) merged while the packet stays in one cell
+    int zero_run = 0;
+    unsigned ray_steps = 0;    // crossings of the current ray since it started or last interacted
+    bool aborted = false;
+
+    auto start_walk = [&]() {
+        tau = -logf(pk.rng.next());
+        ray_steps = 0;
+        zero_run = 0;
+        mode = M_WALK;
+    };
+    // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction)
+    auto start_peel = [&](int ob) {
+        pk.r = saved;
+        pk.r.p = porg;
+        set_dir(pk.r, make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2)));
+        tau = 0.f;
+        ray_steps = 0;
+        zero_run = 0;
+        mode = M_PEEL;
+        if (prelocate && !grid_locate<G>(g, pk.r)) mode = M_PEEL_DONE;
+    };
+    // after an emission or interaction: peel (if wanted) then draw a new optical depth
+    auto after_event = [&](int kind, int relocate) {
+        if (a.peel && pk.sbin >= 0 && o.nobs > 0) {
+            saved = pk.r;
+            pkind = kind;
+            prelocate = relocate;
+            pobs = 0;
+            start_peel(0);
+        } else {
+            start_walk();
+        }
+    };
+    // Watchdog (warp-uniform call): past the time budget, every live lane stops, records its
+    // state in the report buffer (first WD_REPORTS lanes) and is counted; nothing traps.
+    unsigned rounds = 0;
+    auto watchdog = [&](unsigned where) {
+        bool ab = false;
+        if (lane == 0) ab = past_deadline(a, t);
+        if (!__shfl_sync(FULL, ab ? 1 : 0, 0)) return;
+        aborted = true;
+        if (mode == M_DONE) return;
+        lc.v[C_WATCHDOG]++;
+        const unsigned slot = atomicAdd(t.report_count, 1u);
+        if (slot < (unsigned)WD_REPORTS) {
+            float* r = t.report + slot * WD_FIELDS;
+            r[0] = (float)mode; r[1] = (float)pk.rng.pkt; r[2] = (float)pk.nint; r[3] = tau;
+            r[4] = pk.r.p.x; r[5] = pk.r.p.y; r[6] = pk.r.p.z;
+            r[7] = pk.r.u.x; r[8] = pk.r.u.y; r[9] = pk.r.u.z;
+            r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
+            r[13] = pk.nu; r[14] = (float)pobs; r[15] = (float)where;
+        }
+        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+        dep_ci = -1;
+        mode = M_DONE;
+    };
+    auto end_packet = [&]() {
+        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+        dep_ci = -1;
+        dep_val = 0.f;
+        lc.v[C_PACKETS_DONE]++;
+        mode = M_NEED;
+    };
+
+    for (;;) {
+        // ------------------------------------------------------------ event phase
+        if (mode == M_KILLED) {
+            end_packet();
+        } else if (mode == M_ESCAPED) {
+            lc.v[C_ESCAPED]++;
+            tally_escape(o, t, pk, st.esc);
+            end_packet();
+        } else if (mode == M_INTERACT) {
+            if (++pk.nint > a.max_interactions) {
+                lc.v[C_KILLED]++;
+                end_packet();
+            } else {
+                lc.v[C_INTERACTIONS]++;
+                const float z = pk.rng.next();
+                if (z > pk.dust.albedo) {
+                    lc.v[C_ABSORB]++;
+                    if (a.terminate_on_absorb) {
+                        lc.v[C_ABSORBED_TERM]++;
+                        end_packet();
+                    } else {
+                        const float u1 = pk.rng.next(), u2 = pk.rng.next();
+                        set_dir(pk.r, isotropic_dir(u1, u2));
+                        const int row = min(max(__ldg(d.emit_row + pk.r.ci), 0), d.nT - 1);   // bounds check
+                        set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
+                        porg = pk.r.p;
+                        after_event(PEEL_ISO, 0);
+                    }
+                } else {
+                    lc.v[C_SCATTER]++;
+                    const float mu = hg_mu(d.g, pk.rng.next());
+                    const float u2 = pk.rng.next();
+                    uin = pk.r.u;
+                    set_dir(pk.r, scatter_dir(uin, mu, u2));
+                    porg = pk.r.p;
+                    after_event(PEEL_HG, 0);
+                }
+            }
+        } else if (mode == M_PEEL_DONE) {
+            const float3 n = pk.r.u;
+            const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
+            const double w = a.eps * (double)(prob * expf(-tau));
+            if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
+            else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
+            if (o.nimg > 0) {
+                const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
+                const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
+                const int ix = (int)floorf((px + o.img_half) * o.img_scale);
+                const int iy = (int)floorf((py + o.img_half) * o.img_scale);
+                if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
+                    for (int l = 0; l < o.nimg; ++l)
+                        if (__ldg(o.img_bin + l) == pk.sbin)
+                            atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
+            }
+            if (++pobs < o.nobs) {
+                start_peel(pobs);
+            } else {
+                pk.r = saved;
+                start_walk();
+            }
+        }
+        // refill: lanes without a packet take the next ids
+        const unsigned need = __ballot_sync(FULL, mode == M_NEED);
+        if (need) {
+            if (!aborted && past_deadline(a, t)) aborted = true;
+            const long long q = fetch(need, lt_mask);
+            if (mode == M_NEED) {
+                if (aborted || q < 0) {
+                    if (aborted && q >= 0) lc.v[C_WATCHDOG]++;
+                    mode = M_DONE;
+                } else if (!emit_packet<G>(g, d, s, o, a, t, st.sed, (int64_t)q, pk, lc, false)) {
+                    lc.v[C_ESCAPED]++;
+                    lc.v[C_PACKETS_DONE]++;
+                } else {
+                    porg = pk.last_origin;
+                    after_event(PEEL_ISO, pk.emit_relocate);
+                }
+            }
+        }
+        const unsigned live = __ballot_sync(FULL, mode != M_DONE);
+        if (live == 0) break;
+        // ------------------------------------------------------------ walk phase
+        const int thr = min(a.regroup, __popc(live));
+        unsigned steps = 0;
+        for (;;) {
+            const unsigned walkers = __ballot_sync(FULL, mode == M_WALK || mode == M_PEEL);
+            if (walkers == 0 || (__popc(walkers) < thr && walkers != live)) break;
+            bool flushing = false;
+            int32_t fci = 0;
+            float fval = 0.f;
+            if (mode == M_WALK || mode == M_PEEL) {
+                int axis, dir;
+                const float l = cell_exit<G>(g, pk.r, axis, dir);
+                const float rho = __ldg(g.rhoL + pk.r.ci);
+                const float k = rho * pk.dust.chi;
+                bool stop = false;
+                if (mode == M_WALK) {
+                    const float dtau = k * l;
+                    float seg = l;
+                    if (tau < dtau) {
+                        seg = tau / k;
+                        stop = true;
+                    } else {
+                        tau -= dtau;
+                    }
+                    if (rho > 0.f) {
+                        const float v = pk.dust.kappa * seg;
+                        if (pk.r.ci == dep_ci) {
+                            dep_val += v;
+                        } else {
+                            flushing = dep_ci >= 0;
+                            fci = dep_ci;
+                            fval = dep_val;
+                            dep_ci = pk.r.ci;
+                            dep_val = v;
+                        }
+                    }
+                    if (stop) {
+                        pk.r.p.x += seg * pk.r.u.x;
+                        pk.r.p.y += seg * pk.r.u.y;
+                        pk.r.p.z += seg * pk.r.u.z;
+                        mode = M_INTERACT;
+                    } else {
+                        lc.v[C_CROSSINGS]++;
+                    }
+                } else {
+                    tau += k * l;
+                    lc.v[C_PEEL_CROSSINGS]++;
+                }
+                if (!stop) {
+                    if (cell_step<G>(g, pk.r, l, axis, dir)) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
+                    if constexpr (G == GRID_SPHERICAL) {
+                        if (!tiny_step(pk.r, l)) zero_run = 0;
+                        else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
+                    }
+                    if (++ray_steps > MAX_WALK_STEPS && (mode == M_WALK || mode == M_PEEL)) {
+                        lc.v[C_STUCK]++;
+                        if (mode == M_WALK) {
+                            lc.v[C_KILLED]++;
+                            mode = M_KILLED;
+                        } else {
+                            tau = F_INF;           // the peel ray is dropped (zero weight)
+                            mode = M_PEEL_DONE;
+                        }
+                    }
+                } else {
+                    ray_steps = 0;
+                }
+            }
+            flush_deposit<WAGG>(t.acc, flushing, fci, fval);
+            if (((++steps) & 4095u) == 0) watchdog(steps);
+        }
+        if (((++rounds) & 255u) == 0) watchdog(rounds);
+    }
+    if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+}
+
+// ---------------------------------------------------------------- one model
+template <int G, bool WAGG>
+__global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
+    const SharedTallies st = shared_tallies(o, a);
+    LocalCounters lc;
+    lc.zero();
+    const unsigned lane = threadIdx.x & 31u;
+    auto fetch = [&](unsigned need, unsigned lt_mask) -> long long {
+        unsigned long long base = 0;
+        const int leader = __ffs(need) - 1;
+        if ((int)lane == leader) base = atomicAdd(a.work_counter, (unsigned long long)__popc(need));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const unsigned long long q = base + __popc(need & lt_mask);
+        return q < (unsigned long long)a.n_packets ? (long long)(a.first_packet + (int64_t)q) : -1ll;
+    };
+    event_loop<G, WAGG>(g, d, s, o, a, t, st, lc, fetch);
+    flush_counters(lc, t.counters);
+    flush_shared(o, a, t, st);
+}
+
+cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched) {
+    if (job.args.n_packets <= 0) return cudaSuccess;
+    Launch ll = l;
+    ll.block = 256;
+    PropagateJob j = job;
+    j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : DEFAULT_REGROUP;
+    *launched += 1;
+    if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true>, j, ll, s);
+    return launch_persistent(k_event<GRID_SPHERICAL, true>, j, ll, s);
+}
+
+// ---------------------------------------------------------------- many models, one launch
+template <int G, bool WAGG>
+__global__ void __launch_bounds__(256, 2) k_event_batch(const BatchModel* __restrict__ models,
+                                                        const BatchChunk* __restrict__ chunks, int nchunks,
+                                                        unsigned* chunk_counter, const BatchState* __restrict__ state,
+                                                        int regroup) {
+    const unsigned lane = threadIdx.x & 31u;
+    const SharedTallies st{nullptr, nullptr};
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = (int)atomicAdd(chunk_counter, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const BatchChunk ch = chunks[c];
+        if (!state[ch.model].active || models[ch.model].g.type != G) continue;
+        const BatchModel& M = models[ch.model];
+        RunArgs a = M.a;
+        a.iter_key = state[ch.model].iteration;
+        a.regroup = regroup;
+        long long cursor = ch.p0;
+        const long long end = ch.p1;
+        auto fetch = [&](unsigned need, unsigned lt_mask) -> long long {
+            const long long q = cursor + __popc(need & lt_mask);
+            cursor += __popc(need);
+            return q < end ? q : -1ll;
+        };
+        LocalCounters lc;
+        lc.zero();
+        event_loop<G, WAGG>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
+        flush_counters(lc, M.t.counters);
+    }
+}
+
+cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const BatchChunk* chunks, int nchunks,
+                                   unsigned* chunk_counter, const BatchState* state, const Launch& l, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : DEFAULT_REGROUP;
+    if (gtype == GRID_CARTESIAN) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<GRID_CARTESIAN, true>, 256, 0);
+        if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
+        k_event_batch<GRID_CARTESIAN, true><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks,
+                                                                                            chunk_counter, state, regroup);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<GRID_SPHERICAL, true>, 256, 0);
+        if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
+        k_event_batch<GRID_SPHERICAL, true><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks,
+                                                                                            chunk_counter, state, regroup);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hrt

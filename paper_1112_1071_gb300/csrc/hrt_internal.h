@@ -33,13 +33,28 @@ cudaError_t launch_stamp(unsigned long long* t0, cudaStream_t s);
 cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
 
+// event.cu: one persistent launch over the (model, packet range) chunks of grid type gtype
+cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const BatchChunk* chunks, int nchunks,
+                                   unsigned* chunk_counter, const BatchState* state, const Launch& l, cudaStream_t s);
+
+// batch_kernels.cu
+cudaError_t launch_batch_begin(const BatchModel* models, BatchState* state, int nmodels, const BatchSeg* segs,
+                               int nsegs, unsigned* chunk_counter, unsigned* hist, int nesc_per_model, cudaStream_t s);
+cudaError_t launch_batch_temperature(const BatchModel* models, BatchState* state, const BatchSeg* segs, int nsegs,
+                                     cudaStream_t s);
+cudaError_t launch_batch_select(const BatchModel* models, BatchState* state, int nmodels, const BatchSeg* segs,
+                                int nsegs, unsigned* hist, cudaStream_t s);
+cudaError_t launch_batch_end(const BatchModel* models, BatchState* state, int nmodels, double q_thres,
+                             double delta_thres, cudaStream_t s);
+
 // temperature.cu
 struct TemperatureJob {
     int32_t gtype;
     int32_t n1, n2, n3;
     int64_t ncells;
     const float* rhoL;
-    const double* acc;
+    const double* acc;   // sum kappa l in the scaled length unit
+    double acc_scale;    // eps L0: acc * acc_scale = sum eps kappa l (cgs)
     const double* va;    // per-axis volume factors: V = va[i] vb[j] vc[k] (cm^3)
     const double* vb;
     const double* vc;

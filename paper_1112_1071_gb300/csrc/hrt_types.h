@@ -123,4 +123,58 @@ struct RunArgs {
     const unsigned long long* t0;  // globaltimer stamp written just before the launch
 };
 
+constexpr int DEFAULT_REGROUP = 12;
+
+// ---------------------------------------------------------------- batched models
+// Device descriptor of one model of a batch: its problem views, tallies and run arguments, and
+// what the temperature update and the convergence select need.
+struct BatchModel {
+    DevGrid g;
+    DevDust d;
+    DevSources s;
+    DevObs o;
+    Tallies t;
+    RunArgs a;
+    const double* va;              // per-axis volume factors
+    const double* vb;
+    const double* vc;
+    const double* E;               // [nT] emission table, its log, log T nodes, T nodes
+    const double* lnE;
+    const double* lnT;
+    const double* Tn;
+    int32_t nT;
+    int32_t quantity;              // 0 T, 1 Adot
+    double* T;
+    double* adot;
+    int32_t* emit_row;
+    unsigned long long* keys;
+    int64_t n_dust;                // cells with dust
+    int64_t krank;                 // rank of the quantile among all keys (cells without dust key 0)
+};
+
+struct BatchChunk {                // packets [p0, p1) of one model
+    int32_t model;
+    int32_t pad;
+    int64_t p0, p1;
+};
+
+struct BatchSeg {                  // cells [c0, c1) of one model
+    int32_t model;
+    int32_t pad;
+    int64_t c0, c1;
+};
+
+// Per-model iteration state kept on the device between graph launches.
+struct BatchState {
+    uint32_t iteration;            // keys the random streams of the next iteration
+    int32_t active;                // 0 once converged
+    int32_t have_Q;
+    int32_t ran;                   // ran in the last launch
+    int32_t converged;
+    int32_t pad;
+    double Q, Q_prev, Delta;
+    unsigned long long prefix, rank;   // radix select of the quantile
+    unsigned long long clamp_low, clamp_high;
+};
+
 }  // namespace hrt

@@ -156,7 +156,7 @@ __device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, con
         }
         const float u1 = pk.rng.next(), u2 = pk.rng.next();
         set_dir(pk.r, isotropic_dir(u1, u2));
-        const int row = __ldg(d.emit_row + pk.r.ci);
+        const int row = min(max(__ldg(d.emit_row + pk.r.ci), 0), d.nT - 1);   // bounds check
         set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
         if (a.peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
     } else {

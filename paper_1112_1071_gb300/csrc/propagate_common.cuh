@@ -1,0 +1,75 @@
+// Helpers shared by the propagation kernels: per-block shared-memory SED and escape tallies,
+// the watchdog test and the persistent launch shape.
+#pragma once
+#include "hrt_internal.h"
+#include "packet.cuh"
+
+namespace hrt {
+
+struct SharedTallies {
+    double* sed;        // [nobs][nsed] or null (then global atomics)
+    unsigned* esc;      // [10][nsed] or null
+};
+
+__device__ __forceinline__ SharedTallies shared_tallies(const DevObs& o, const RunArgs& a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedTallies st{nullptr, nullptr};
+    if (a.smem_sed) {
+        st.sed = reinterpret_cast<double*>(smem_raw);
+        st.esc = reinterpret_cast<unsigned*>(smem_raw + sizeof(double) * (size_t)o.nobs * o.nsed);
+        for (int i = threadIdx.x; i < o.nobs * o.nsed; i += blockDim.x) st.sed[i] = 0.0;
+        for (int i = threadIdx.x; i < N_ESC_MU * o.nsed; i += blockDim.x) st.esc[i] = 0u;
+    }
+    __syncthreads();
+    return st;
+}
+
+__device__ __forceinline__ void flush_shared(const DevObs& o, const RunArgs& a, const Tallies& t,
+                                             const SharedTallies& st) {
+    __syncthreads();
+    if (!a.smem_sed) return;
+    for (int i = threadIdx.x; i < o.nobs * o.nsed; i += blockDim.x)
+        if (st.sed[i] != 0.0) atomicAdd(t.sed + i, st.sed[i]);
+    for (int i = threadIdx.x; i < N_ESC_MU * o.nsed; i += blockDim.x)
+        if (st.esc[i]) atomicAdd(t.esc + i, (unsigned long long)st.esc[i]);
+}
+
+// Watchdog: a kernel past its time budget raises the abort flag and every thread stops at its
+// next check (no trap; the host reports HRT_ETIMEDOUT and the context stays usable).
+__device__ __forceinline__ bool past_deadline(const RunArgs& a, const Tallies& t) {
+    if (a.budget_ns == 0) return false;
+    if (*(volatile int32_t*)t.abort_flag) return true;
+    if (global_ns() > *a.t0 + a.budget_ns) {
+        atomicExch(t.abort_flag, 1);
+        return true;
+    }
+    return false;
+}
+
+inline size_t shared_bytes(const PropagateJob& job) {
+    if (!job.args.smem_sed) return 0;
+    return sizeof(double) * (size_t)job.obs.nobs * job.obs.nsed + sizeof(unsigned) * (size_t)N_ESC_MU * job.obs.nsed;
+}
+
+// Persistent launch: blocks_per_sm (or the occupancy limit) blocks on every SM, fewer when
+// there are fewer packets than threads.
+template <typename K>
+inline cudaError_t launch_persistent(K kernel, const PropagateJob& job, const Launch& l, cudaStream_t s) {
+    const size_t smem = shared_bytes(job);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, l.block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
+    int blocks = l.blocks > 0 ? l.blocks : per_sm * sms;
+    const int64_t need = (job.args.n_packets + l.block - 1) / l.block;
+    if (need < blocks) blocks = (int)(need > 0 ? need : 1);
+    kernel<<<blocks, l.block, smem, s>>>(job.grid, job.dust, job.src, job.obs, job.args, job.tal);
+    return cudaGetLastError();
+}
+
+}  // namespace hrt

@@ -1,43 +1,13 @@
 // Temperature update and convergence statistic of a Lucy iteration (FP64).
 //
-// Sect. 2.3, Eq. 2: Adot = acc / (V dt), dt = 1 s, acc = sum eps kappa l over the iteration.
-// Sect. 2.3, Eq. 3: T from 4 pi kappa_P(T) B(T) = Adot, inverted on the tabulated
-//   E(T_m) = 4 pi int kappa_nu B_nu(T_m) dnu by bisection and log-log interpolation, clamped
-//   (and counted) at the table ends.
-// Sect. 2.4, Eqs. 4-5: R = delta(prev, new) = max(prev/new, new/prev) per cell with dust; the
-//   p-quantile Q is the exact nearest-rank order statistic, found by an 8-pass radix select on
-//   the IEEE-754 bit patterns of R (positive doubles sort like their bit patterns).
+// Sect. 2.3, Eqs. 2-3: per cell Adot = acc/(V dt) and T from the tabulated E(T) (temperature.cuh).
+// Sect. 2.4, Eqs. 4-5: R = delta(prev, new) per cell with dust; the p-quantile Q is the exact
+//   nearest-rank order statistic, found by an 8-pass radix select on the IEEE-754 bit patterns
+//   of R (positive doubles sort like their bit patterns).
 #include "hrt_internal.h"
+#include "temperature.cuh"
 
 namespace hrt {
-
-__device__ __forceinline__ double invert_E(double A, const double* __restrict__ E, const double* __restrict__ lnE,
-                                           const double* __restrict__ lnT, const double* __restrict__ Tn, int nT,
-                                           int& clamp) {
-    clamp = 0;
-    if (!(A > E[0])) { clamp = -1; return Tn[0]; }
-    if (A >= E[nT - 1]) { clamp = 1; return Tn[nT - 1]; }
-    int lo = 0, hi = nT - 1;   // E[lo] <= A < E[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (E[mid] <= A) lo = mid; else hi = mid;
-    }
-    const double f = (log(A) - lnE[lo]) / (lnE[lo + 1] - lnE[lo]);
-    return exp(lnT[lo] + f * (lnT[lo + 1] - lnT[lo]));
-}
-
-// Table row for re-emission: nearest temperature node in log T, ties to the lower node.
-__device__ __forceinline__ int32_t nearest_row(double T, const double* __restrict__ lnT, int nT) {
-    const double x = log(T);
-    if (x <= lnT[0]) return 0;
-    if (x >= lnT[nT - 1]) return nT - 1;
-    int lo = 0, hi = nT - 1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (lnT[mid] <= x) lo = mid; else hi = mid;
-    }
-    return (lnT[lo + 1] - x) < (x - lnT[lo]) ? lo + 1 : lo;
-}
 
 constexpr int MAX_T_SMEM = 1024;   // four FP64 tables: 32 KB of static shared memory
 
@@ -59,27 +29,16 @@ __global__ void __launch_bounds__(256) k_temperature(TemperatureJob j) {
         const int i = (int)(c % j.n1);
         const int jj = (int)((c / j.n1) % j.n2);
         const int k = (int)(c / ((int64_t)j.n1 * j.n2));
-        const double V = j.va[i] * j.vb[jj] * j.vc[k];
-        const double A = j.acc[c] / V;                       // Eq. 2 with dt = 1 s
         int cl;
-        const double Tnew = invert_E(A, E, lnE, lnT, Tn, j.nT, cl);   // Eq. 3
-        const double Told = j.T[c];
-        const double Aold = j.adot[c];
-        const bool dust = j.rhoL[c] > 0.f;
-        unsigned long long key = 0ull;
-        if (dust) {
-            lo_c += cl < 0;
-            hi_c += cl > 0;
-            double R;
-            if (j.quantity == 0) R = fmax(Told / Tnew, Tnew / Told);
-            else R = j.first ? __longlong_as_double(0x7ff0000000000000ll) : fmax(Aold / A, A / Aold);
-            if (!(R == R)) R = __longlong_as_double(0x7ff0000000000000ll);   // 0/0: treat as infinite change
-            key = (unsigned long long)__double_as_longlong(R);
-        }
-        j.T[c] = Tnew;
+        double T = j.T[c], A = j.adot[c];
+        int32_t row;
+        j.keys[c] = temperature_cell(j.acc[c] * j.acc_scale, j.va[i] * j.vb[jj] * j.vc[k], j.rhoL[c] > 0.f, j.quantity, j.first != 0,
+                                     E, lnE, lnT, Tn, j.nT, T, A, row, cl);
+        j.T[c] = T;
         j.adot[c] = A;
-        j.emit_row[c] = nearest_row(Tnew, lnT, j.nT);
-        j.keys[c] = key;
+        j.emit_row[c] = row;
+        lo_c += cl < 0;
+        hi_c += cl > 0;
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo_c += __shfl_down_sync(0xffffffffu, lo_c, o);

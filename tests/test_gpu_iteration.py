@@ -117,6 +117,17 @@ def test_peeloff_sed_and_image_match_oracle(kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+def test_peeloff_pass_on_a_fresh_context(kernel):
+    # the re-emission rows come from the starting temperatures even before any Lucy iteration
+    wl = W.tiny_sphere(n_packets=20000)
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    m.run_iteration(kernel=kernel, peel=1, update_temperature=0)
+    ref = om.run_iteration(peel=True, update=False, nthreads=8)
+    np.testing.assert_allclose(m.sed().sum(axis=1), ref["sed"].sum(axis=1), rtol=1e-3)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_grey_slab_first_flight_closed_form(kernel):
     tau = 1.0
     wl = W.slab(n_layers=8, tau_total=tau, albedo=0.0, n_packets=200_000)
@@ -192,8 +203,10 @@ def test_event_kernel_reproduces_plain_histories(name):
         st = m.run_iteration(kernel=hrt.HRT_KERNEL_EVENT, regroup_threshold=regroup)
         runs.append(m.absorbed())
         if name == "tiny_sphere":
-            # identical FP32 arithmetic in both kernels: same histories, sums differ in order only
-            np.testing.assert_allclose(runs[-1], acc0, rtol=1e-9, atol=1e-300)
+            # identical FP32 arithmetic in both kernels: same histories; the event kernel merges
+            # a lane's FP32 kappa*l products within a cell before its FP64 atomic, the plain
+            # kernel adds each product alone, so sums differ at FP32 rounding (< 1e-6)
+            np.testing.assert_allclose(runs[-1], acc0, rtol=1e-6, atol=1e-300)
             for k in ("n_crossings", "n_interactions", "n_scatter", "n_absorb", "e_escaped"):
                 assert st[k] == sp[k], (regroup, k)
         else:
@@ -203,9 +216,9 @@ def test_event_kernel_reproduces_plain_histories(name):
             rel = np.abs(runs[-1][seen] - acc0[seen]) / acc0[seen]
             assert np.median(rel) < 1e-5
             assert st["n_crossings"] == pytest.approx(sp["n_crossings"], rel=1e-3)
-    # the launch shape of the event kernel never changes a history
+    # the launch shape of the event kernel never changes a history (only the FP32 merge order)
     for r in runs[1:]:
-        np.testing.assert_allclose(r, runs[0], rtol=1e-9, atol=1e-300)
+        np.testing.assert_allclose(r, runs[0], rtol=1e-6, atol=1e-300)
     # imaging pass: SEDs agree as well
     ref.run_iteration(kernel=hrt.HRT_KERNEL_PLAIN, peel=1, update_temperature=0, n_packets=5000)
     m = hrt.Model(wl)
