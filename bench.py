@@ -289,6 +289,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(args, world),
             "time_to_converged_ms": statistics.median(done) if done else None,
+            "q99_history": [round(s["Q"], 5) for s in last[:-1]],
             "iterations_to_converged": statistics.median([i for i in its if i]) if any(its) else None,
             "crossings_per_step": sum(s["n_crossings"] for s in last),
             "peel_crossings_per_step": sum(s["n_peel_crossings"] for s in last),

@@ -100,17 +100,16 @@ __device__ __forceinline__ bool cart_locate(const DevGrid& g, Ray& r) {
 }
 
 // ================================================================ spherical-polar
+// uR2 = u_x^2 + u_y^2, pu = p_x u_x + p_y u_y and Rp = |p_R| are shared by both cones of a cell.
 template <typename R>
-__device__ __forceinline__ R cone_root(R px, R py, R pz, R ux, R uy, R uz, R cw, R sw, int sense, R tol) {
+__device__ __forceinline__ R cone_root(R px, R py, R pz, R ux, R uy, R uz, R uR2, R pu, R Rp, R cw, R sw, int sense,
+                                       R tol) {
     const R inf = R(F_INF);
     if (cw == R(0)) {          // the midplane z = 0; f = z increases when u_z > 0
         if (uz == R(0) || ((sense > 0) != (uz > R(0)))) return inf;
         const R s = -pz / uz;
         return s < -tol ? inf : (s > R(0) ? s : R(0));
     }
-    const R uR2 = ux * ux + uy * uy;
-    const R pu = px * ux + py * uy;
-    const R Rp = sqrt(px * px + py * py);
     const R sw2 = sw * sw, cw2 = cw * cw;
     const R A = uz * uz * sw2 - uR2 * cw2;
     const R B = pz * uz * sw2 - pu * cw2;
@@ -131,9 +130,10 @@ __device__ __forceinline__ R cone_root(R px, R py, R pz, R ux, R uy, R uz, R cw,
         const R qz = pz + s * uz;
         if (!(qz * cw > R(0))) continue;        // other nappe
         const R qx = px + s * ux, qy = py + s * uy;
-        const R Rq = sqrt(qx * qx + qy * qy);
-        if (Rq == R(0)) continue;
-        const R dfds = uz * sw - cw * (qx * ux + qy * uy) / Rq;
+        const R Rq2 = qx * qx + qy * qy;
+        if (Rq2 == R(0)) continue;
+        // sign of df/ds = u_z sin - cos (q_R . u_R) / |q_R|, scaled by |q_R| > 0 (no division)
+        const R dfds = uz * sw * sqrt(Rq2) - cw * (qx * ux + qy * uy);
         if (sense > 0 ? !(dfds > R(0)) : !(dfds < R(0))) continue;
         best = s > R(0) ? s : R(0);
     }
@@ -171,6 +171,19 @@ __device__ __forceinline__ float phi_root(const Ray& r, float cw, float sw, int 
     return fmaxf(s, 0.f);
 }
 
+// Exit through cone wall jw in the given sense; FP64 for walls near the polar axis.
+__device__ __forceinline__ float cone_wall(const DevGrid& g, const Ray& r, int jw, int sense, float uR2, float pu,
+                                          float Rp, float tol) {
+    const float sw = __ldg(g.sth + jw);
+    if (sw < g.sin_fp64) {
+        const double px = r.p.x, py = r.p.y, ux = r.u.x, uy = r.u.y;
+        return (float)cone_root<double>(px, py, r.p.z, ux, uy, r.u.z, ux * ux + uy * uy, px * ux + py * uy,
+                                        sqrt(px * px + py * py), __ldg(g.cthd + jw), __ldg(g.sthd + jw), sense,
+                                        (double)tol);
+    }
+    return cone_root<float>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, uR2, pu, Rp, __ldg(g.cth + jw), sw, sense, tol);
+}
+
 // Distance to the exit of the current cell; axis 0/1/2 = r/theta/phi, dir = +-1.
 __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& axis, int& dir) {
     const float rr = dot3(r.p, r.p);
@@ -201,24 +214,17 @@ __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& a
             if (s < best) { best = s; dir = -1; }
         }
     }
+    // terms shared by both cones of the cell
+    const float uR2 = r.u.x * r.u.x + r.u.y * r.u.y;
+    const float pu = r.p.x * r.u.x + r.p.y * r.u.y;
+    const float Rp = sqrtf(r.p.x * r.p.x + r.p.y * r.p.y);
+    // lower wall j is left with theta decreasing (sense +1), upper wall j + 1 increasing (-1)
     if (r.j > 0) {
-        const float sw = __ldg(g.sth + r.j);
-        float s;
-        if (sw < g.sin_fp64)
-            s = (float)cone_root<double>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, __ldg(g.cthd + r.j),
-                                         __ldg(g.sthd + r.j), +1, (double)tol);
-        else
-            s = cone_root<float>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, __ldg(g.cth + r.j), sw, +1, tol);
+        const float s = cone_wall(g, r, r.j, +1, uR2, pu, Rp, tol);
         if (s < best) { best = s; axis = 1; dir = -1; }
     }
     if (r.j + 1 < g.n2) {
-        const float sw = __ldg(g.sth + r.j + 1);
-        float s;
-        if (sw < g.sin_fp64)
-            s = (float)cone_root<double>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, __ldg(g.cthd + r.j + 1),
-                                         __ldg(g.sthd + r.j + 1), -1, (double)tol);
-        else
-            s = cone_root<float>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, __ldg(g.cth + r.j + 1), sw, -1, tol);
+        const float s = cone_wall(g, r, r.j + 1, -1, uR2, pu, Rp, tol);
         if (s < best) { best = s; axis = 1; dir = 1; }
     }
     if (g.n3 > 1) {

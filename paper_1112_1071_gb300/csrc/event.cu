@@ -24,6 +24,9 @@ namespace hrt {
 
 enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE };
 
+// Optical depth beyond which a peel-off ray stops: exp(-40) = 4e-18 of its weight remains.
+constexpr float PEEL_TAU_STOP = 40.f;
+
 // Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
 // With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
 // group adds its sum with one FP64 atomic.
@@ -257,6 +260,8 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 } else {
                     tau += k * l;
                     lc.v[C_PEEL_CROSSINGS]++;
+                    // a peel ray behind more than PEEL_TAU_STOP carries < 4e-18 of its weight
+                    if (tau > PEEL_TAU_STOP) stop = true, mode = M_PEEL_DONE;
                 }
                 if (!stop) {
                     if (cell_step<G>(g, pk.r, l, axis, dir)) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
@@ -287,8 +292,9 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
 }
 
 // ---------------------------------------------------------------- one model
-template <int G, bool WAGG>
-__global__ void __launch_bounds__(256, 2) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
+// MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80)
+template <int G, bool WAGG, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
     const SharedTallies st = shared_tallies(o, a);
     LocalCounters lc;
     lc.zero();
@@ -313,8 +319,15 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     PropagateJob j = job;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : DEFAULT_REGROUP;
     *launched += 1;
-    if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true>, j, ll, s);
-    return launch_persistent(k_event<GRID_SPHERICAL, true>, j, ll, s);
+    // default shape (measured on GB300): the Cartesian walk gains from 3 blocks/SM at 80
+    // registers, the spherical walk needs the 128-register budget of 2 blocks/SM
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (job.grid.type == GRID_CARTESIAN ? 3 : 2);
+    if (bps >= 3) {
+        if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true, 3>, j, ll, s);
+        return launch_persistent(k_event<GRID_SPHERICAL, true, 3>, j, ll, s);
+    }
+    if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true, 2>, j, ll, s);
+    return launch_persistent(k_event<GRID_SPHERICAL, true, 2>, j, ll, s);
 }
 
 // ---------------------------------------------------------------- many models, one launch
