@@ -220,6 +220,48 @@ int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* 
 /* Tabulated E(T) [nT] and emissivity cdf [nT][nnu] as built on the device (copied to host). */
 int hrt_get_tables(hrt_ctx* ctx, double* E, int64_t nE, float* cdf, int64_t ncdf);
 
+/* ------------------------------------------------------------------ learned warm start
+ * Not in the paper: a 3-D convolutional encoder-decoder (U-Net) trained on temperature fields
+ * that the Monte-Carlo iteration itself produced, used only to start the iteration closer to its
+ * fixed point; the Lucy iteration and its convergence test (Sect. 2.3-2.4) stay the judge.
+ * Levels L (1-4), base width c (multiple of 32): per level two 3x3x3 conv+ReLU and 2x average
+ * pooling, a bottleneck of width c 2^L, a mirrored decoder (2x nearest upsampling concatenated
+ * with the encoder skip, two conv+ReLU) and a 1x1x1 head.  Weights are FP32 masters (Adam) with
+ * BF16 copies; activations BF16; every convolution runs on the tensor cores with FP32
+ * accumulation.  Tensors are channels-last [N][D][H][W][C] float32 on the device.
+ * Inputs: 2 channels, (log10 rho[g/cm^3] + 21.5) / 1 and log10(F[erg/s/cm^2]) / 2 with F the
+ * summed point-source flux L/(4 pi (d^2 + (dx/2)^2)) at the cell centre (hrt_net_features).
+ * Output: y = (log10 T[K] - 1.5) / 0.5.  D, H, W must be multiples of 2^L. */
+typedef struct hrt_net hrt_net;
+int hrt_net_create(hrt_net** out, int device, int base_channels, int levels, uint64_t seed, void* stream);
+int hrt_net_destroy(hrt_net* net);
+/* Parameters in packed order: per conv layer W[27][Cin][Cout] (tap = 9 dz + 3 dy + dx) then
+ * b[Cout]; then the head w[c], b[1].  */
+int64_t hrt_net_num_params(const hrt_net* net);
+int hrt_net_get_params(hrt_net* net, float* host_out, int64_t n);
+int hrt_net_set_params(hrt_net* net, const float* host_in, int64_t n);
+/* d_out[N][D][H][W] = network(d_in[N][D][H][W][2]); blocks until done. */
+int hrt_net_forward(hrt_net* net, int N, int D, int H, int W, const float* d_in, float* d_out);
+/* Loss 0.5 mean((y - target)^2) and its gradient (packed order, host buffer). */
+int hrt_net_gradients(hrt_net* net, int N, int D, int H, int W, const float* d_in, const float* d_target,
+                      float* host_grad, int64_t n, double* loss);
+/* One Adam step (beta 0.9, 0.999) on that loss; *loss (may be NULL) is the loss before the step. */
+int hrt_net_train_step(hrt_net* net, int N, int D, int H, int W, const float* d_in, const float* d_target, float lr,
+                       double* loss);
+/* Input features of a Cartesian context (2 floats per cell, device). */
+int hrt_net_features(hrt_ctx* ctx, float* d_out, int64_t n);
+/* Training target of a context: its current temperatures as y (1 float per cell, device). */
+int hrt_net_temperature_target(hrt_ctx* ctx, float* d_out, int64_t n);
+/* Replace the context's temperatures by the network's prediction (clamped to the T table). */
+int hrt_net_warm_start(hrt_net* net, hrt_ctx* ctx);
+/* Single-layer hooks on FP32 device tensors (converted to BF16 inside): 'same' 3x3x3 conv with
+ * bias and optional ReLU (Cin % 16 == 0, Cout % 32 == 0), and its input, weight and bias
+ * gradients for an output gradient dy (Cin, Cout % 32 == 0).  Weights [27][Cin][Cout]. */
+int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
+                  int relu, float* d_y, void* stream);
+int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                           const float* d_dy, float* d_dx, float* d_dw, float* d_db, void* stream);
+
 /* ------------------------------------------------------------------ allocation-free quantile
  * The paper has no counterpart: this is a convenience for callers of the library that cannot
  * allocate device memory, such as a host framework whose allocator already owns the device's

@@ -103,6 +103,21 @@ _SIGS = {
     "hrt_step_temperature": (C.c_int, [_vp, _i64, _vp, _vp]),
     "hrt_get_tables": (C.c_int, [_vp, _vp, _i64, _vp, _i64]),
     "hrt_quantile_ratio_noalloc": (C.c_int, [_i64, _vp, _vp, _vp, C.c_double, _vp, _vp]),
+    "hrt_net_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_uint64, _vp]),
+    "hrt_net_destroy": (C.c_int, [_vp]),
+    "hrt_net_num_params": (C.c_int64, [_vp]),
+    "hrt_net_get_params": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_net_set_params": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_net_forward": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "hrt_net_gradients": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _i64,
+                                    C.POINTER(C.c_double)]),
+    "hrt_net_train_step": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, C.c_float,
+                                     C.POINTER(C.c_double)]),
+    "hrt_net_features": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_net_temperature_target": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_net_warm_start": (C.c_int, [_vp, _vp]),
+    "hrt_nn_conv3d": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "hrt_nn_conv3d_backward": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hrt_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int]),
     "hrt_batch_destroy": (C.c_int, [_vp]),
     "hrt_batch_run": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(hrt_run_params), _vp, C.POINTER(C.c_int)]),
