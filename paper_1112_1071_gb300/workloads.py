@@ -256,12 +256,13 @@ def turbulent_cloud(n: int = 256, box_pc: float = 0.65, sigma_lnrho: float = 1.5
         n_packets=n_packets, n_iter=n_iter, seed=seed)
 
 
-def warmstart_cloud(seed: int, n: int = 128, n_packets: int = 4_000_000, n_iter: int = 12) -> Workload:
+def warmstart_cloud(seed: int, n: int = 128, n_packets: int = 4_000_000, n_iter: int = 12,
+                    tau_mean_550: float = 10.0) -> Workload:
     """128^3 cloud as ``turbulent_cloud`` with 1-8 sources (training / held-out fields)."""
     rng = np.random.default_rng(seed)
     ns = int(rng.integers(1, 9))
     wl = turbulent_cloud(n=n, n_sources=ns, n_packets=n_packets, n_iter=n_iter, seed=seed, img_n=0,
-                         img_lam_um=())
+                         img_lam_um=(), tau_mean_550=tau_mean_550)
     wl.name = f"warmstart{seed}"
     return wl
 
