@@ -75,13 +75,14 @@ int stage_grid(hrt_ctx* ctx) {
         for (int k = 0; k < ctx->n[2]; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
     } else {
         const int nr = ctx->n[0], nt = ctx->n[1], np = ctx->n[2];
-        std::vector<float> rw(nr + 1), r2w(nr + 1), thw(nt + 1), cth(nt + 1), sth(nt + 1), phw(np + 1), cph(np + 1),
+        std::vector<float> rw(nr + 1), r2w(nr + 1), r2wl(nr + 1), thw(nt + 1), cth(nt + 1), sth(nt + 1), phw(np + 1), cph(np + 1),
             sph(np + 1);
         std::vector<double> rwd(nr + 1), cthd(nt + 1), sthd(nt + 1);
         for (int i = 0; i <= nr; ++i) {
             rwd[i] = ctx->w[0][i] / ctx->L0;
             rw[i] = (float)rwd[i];
             r2w[i] = (float)(rwd[i] * rwd[i]);
+            r2wl[i] = (float)(rwd[i] * rwd[i] - (double)r2w[i]);
         }
         for (int j = 0; j <= nt; ++j) {
             const double t = ctx->w[1][j];
@@ -99,6 +100,7 @@ int stage_grid(hrt_ctx* ctx) {
         }
         CK(ctx->d_rw.upload(rw.data(), rw.size(), s), "walls");
         CK(ctx->d_r2w.upload(r2w.data(), r2w.size(), s), "walls");
+        CK(ctx->d_r2wl.upload(r2wl.data(), r2wl.size(), s), "walls");
         CK(ctx->d_rwd.upload(rwd.data(), rwd.size(), s), "walls");
         CK(ctx->d_thw.upload(thw.data(), thw.size(), s), "walls");
         CK(ctx->d_cth.upload(cth.data(), cth.size(), s), "walls");
@@ -108,12 +110,12 @@ int stage_grid(hrt_ctx* ctx) {
         CK(ctx->d_phw.upload(phw.data(), phw.size(), s), "walls");
         CK(ctx->d_cph.upload(cph.data(), cph.size(), s), "walls");
         CK(ctx->d_sph.upload(sph.data(), sph.size(), s), "walls");
-        g.rw = ctx->d_rw.p; g.r2w = ctx->d_r2w.p; g.rwd = ctx->d_rwd.p;
+        g.rw = ctx->d_rw.p; g.r2w = ctx->d_r2w.p; g.r2wl = ctx->d_r2wl.p; g.rwd = ctx->d_rwd.p;
         g.thw = ctx->d_thw.p; g.cth = ctx->d_cth.p; g.sth = ctx->d_sth.p; g.cthd = ctx->d_cthd.p; g.sthd = ctx->d_sthd.p;
         g.phw = ctx->d_phw.p; g.cph = ctx->d_cph.p; g.sph = ctx->d_sph.p;
         g.r0 = rw[0];
-        // FP64 sphere solves for the shells within 25% of the inner radius (or of the first
-        // wall without a hole); elsewhere the stable root forms are accurate in FP32
+        // FP64 sphere coefficients for the shells within 25% of the inner radius (or of the
+        // first wall without a hole), FP64 cone coefficients within sin(theta) < 0.1 of the axis
         g.r_fp64 = (float)(1.25 * (rwd[0] > 0 ? rwd[0] : rwd[1]));
         g.sin_fp64 = 0.1f;
         for (int i = 0; i < nr; ++i) va[i] = (std::pow(ctx->w[0][i + 1], 3) - std::pow(ctx->w[0][i], 3)) / 3.0;
@@ -269,6 +271,8 @@ int stage_observers(hrt_ctx* ctx) {
     const double den = std::log(lmax / lmin);
     O.sed_b = ctx->nsed / den;
     O.sed_a = ctx->nsed * (std::log(C_LIGHT_CGS) - std::log(lmin)) / den;
+    O.sed_af = (float)O.sed_a;
+    O.sed_bf = (float)O.sed_b;
     O.img_half = (float)(ctx->img_half / ctx->L0);
     O.img_scale = ctx->img_half > 0 ? (float)(ctx->img_nx / (2.0 * ctx->img_half / ctx->L0)) : 0.f;
     O.img_bin = ctx->d_img_bin.p;
@@ -336,7 +340,7 @@ int hrt_destroy(hrt_ctx* ctx) {
     if (!ctx) return HRT_EINVAL;
     DeviceGuard dg(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto* b : {&ctx->d_rhoL, &ctx->d_w1, &ctx->d_w2, &ctx->d_w3, &ctx->d_rw, &ctx->d_r2w, &ctx->d_thw, &ctx->d_cth,
+    for (auto* b : {&ctx->d_rhoL, &ctx->d_w1, &ctx->d_w2, &ctx->d_w3, &ctx->d_rw, &ctx->d_r2w, &ctx->d_r2wl, &ctx->d_thw, &ctx->d_cth,
                     &ctx->d_sth, &ctx->d_phw, &ctx->d_cph, &ctx->d_sph, &ctx->d_lnu, &ctx->d_inv_dlnu, &ctx->d_lchi,
                     &ctx->d_alb, &ctx->d_nuf, &ctx->d_cdf_emit, &ctx->d_src_pos, &ctx->d_spec_nu, &ctx->d_spec_cdf,
                     &ctx->d_obs_n, &ctx->d_obs_ex, &ctx->d_obs_ey})

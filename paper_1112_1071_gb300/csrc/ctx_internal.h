@@ -87,7 +87,7 @@ struct hrt_ctx {
     bool dirty_grid = true, dirty_dust = true, dirty_src = true, dirty_obs = true, have_T = false;
 
     // ---- device problem
-    DBuf<float> d_rhoL, d_w1, d_w2, d_w3, d_rw, d_r2w, d_thw, d_cth, d_sth, d_phw, d_cph, d_sph;
+    DBuf<float> d_rhoL, d_w1, d_w2, d_w3, d_rw, d_r2w, d_r2wl, d_thw, d_cth, d_sth, d_phw, d_cph, d_sph;
     DBuf<double> d_rwd, d_cthd, d_sthd, d_va, d_vb, d_vc;
     DBuf<float> d_lnu, d_inv_dlnu, d_lchi, d_alb, d_nuf, d_cdf_emit;
     DBuf<double> d_nu, d_kappa, d_Tn, d_lnT, d_E, d_lnE;

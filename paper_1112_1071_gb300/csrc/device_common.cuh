@@ -150,4 +150,18 @@ __device__ __forceinline__ float3 scatter_dir(float3 u, float mu, float u2) {
 
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// FP32 -> FP64 widening by integer operations (exact for normal numbers: the exponent is
+// rebiased by 1023 - 127 and the 23 fraction bits move up by 29), so that the deposit atomics
+// of the walk do not occupy the FP64 pipe; zero, subnormals, infinities and NaN take the
+// ordinary conversion.
+__device__ __forceinline__ double widen(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e - 1u >= 254u) return (double)v;
+    const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 }  // namespace hrt

@@ -11,8 +11,7 @@
 // wall is admissible only when the ray leaves the cell through it (r increasing through the
 // outer sphere, decreasing through the inner one; theta decreasing through the lower cone,
 // increasing through the upper; phi likewise), which makes the walk robust for packets sitting
-// on a wall.  Sphere solves for small radii and cone solves near the polar axis run in FP64;
-// everything else in FP32.
+// on a wall.  The precision policy of the wall solves is stated with them below.
 #pragma once
 #include "device_common.cuh"
 
@@ -100,64 +99,122 @@ __device__ __forceinline__ bool cart_locate(const DevGrid& g, Ray& r) {
 }
 
 // ================================================================ spherical-polar
-// uR2 = u_x^2 + u_y^2, pu = p_x u_x + p_y u_y and Rp = |p_R| are shared by both cones of a cell.
-template <typename R>
-__device__ __forceinline__ R cone_root(R px, R py, R pz, R ux, R uy, R uz, R uR2, R pu, R Rp, R cw, R sw, int sense,
-                                       R tol) {
-    const R inf = R(F_INF);
-    if (cw == R(0)) {          // the midplane z = 0; f = z increases when u_z > 0
-        if (uz == R(0) || ((sense > 0) != (uz > R(0)))) return inf;
-        const R s = -pz / uz;
-        return s < -tol ? inf : (s > R(0) ? s : R(0));
-    }
-    const R sw2 = sw * sw, cw2 = cw * cw;
-    const R A = uz * uz * sw2 - uR2 * cw2;
-    const R B = pz * uz * sw2 - pu * cw2;
-    const R f = pz * sw - Rp * cw;              // r sin(theta_w - theta): > 0 above the cone
-    const R C = f * (pz * sw + Rp * cw);
-    const R disc = B * B - A * C;
-    if (disc < R(0)) return inf;
-    const R sq = sqrt(disc);
-    const R q = -(B + copysign(sq, B));
-    R roots[2];
-    roots[0] = (A != R(0)) ? q / A : inf;
-    roots[1] = (q != R(0)) ? C / q : inf;
-    R best = inf;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const R s = roots[t];
-        if (!(s >= -tol) || !(s < best)) continue;
-        const R qz = pz + s * uz;
-        if (!(qz * cw > R(0))) continue;        // other nappe
-        const R qx = px + s * ux, qy = py + s * uy;
-        const R Rq2 = qx * qx + qy * qy;
-        if (Rq2 == R(0)) continue;
-        // sign of df/ds = u_z sin - cos (q_R . u_R) / |q_R|, scaled by |q_R| > 0 (no division)
-        const R dfds = uz * sw * sqrt(Rq2) - cw * (qx * ux + qy * uy);
-        if (sense > 0 ? !(dfds > R(0)) : !(dfds < R(0))) continue;
-        best = s > R(0) ? s : R(0);
-    }
-    return best;
+// Precision of the wall solves.  Positions and directions are FP32; the distance returned is
+// FP32.  What FP32 arithmetic loses is the cancellation in the quadratic's terms when they
+// nearly vanish: |p|^2 - r_w^2 for a point close to a sphere, and the discriminant for a ray
+// nearly tangent to a sphere or a cone (the root error grows as the rounding of those terms
+// divided by the root separation).  So:
+//   * |p|^2 - r_w^2 is formed in FP32 with the rounding errors of the squares and sums carried
+//     (error-free transformations) against r_w^2 held as an FP32 pair: ~2^-44 |p|^2 instead of
+//     2^-23 |p|^2, at the cost of ~20 FP32 operations and no FP64;
+//   * the coefficients and discriminant are formed in FP64 (products of FP32 numbers are exact
+//     in FP64, so only their sums round) for spheres below r_fp64 and cones with sin(theta)
+//     below sin_fp64 (small r and the polar axis), and for any sphere or cone whose FP32
+//     discriminant is within 2^-10 of a double root (a grazing ray).  The square root,
+//     divisions and root selection then run in FP32 on the accurately rounded coefficients.
+
+// s = a + b exactly as s + e (Knuth); __fadd_rn keeps the compiler from fusing or reordering.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// outer sphere: the far root (always ahead of a point inside); inner sphere: the near root,
-// only while moving inwards.
-template <typename R>
-__device__ __forceinline__ R sphere_out(R rr, R b, R rw2) {
-    const R c = rr - rw2;
-    const R disc = b * b - c;
-    const R sq = sqrt(disc > R(0) ? disc : R(0));
-    // far root without cancellation: -c / (b + sq) when moving outwards, -b + sq otherwise
-    const R s = b > R(0) ? -c / (b + sq) : -b + sq;
-    return s > R(0) ? s : R(0);
+// |p|^2 - (w_hi + w_lo) with the FP32 rounding errors of the squares (fma) and sums carried.
+__device__ __forceinline__ float sphere_c(float3 p, float w_hi, float w_lo) {
+    const float x2 = __fmul_rn(p.x, p.x), y2 = __fmul_rn(p.y, p.y), z2 = __fmul_rn(p.z, p.z);
+    const float ex = fmaf(p.x, p.x, -x2), ey = fmaf(p.y, p.y, -y2), ez = fmaf(p.z, p.z, -z2);
+    float s1, e1, s2, e2, s3, e3;
+    two_sum(x2, y2, s1, e1);
+    two_sum(s1, z2, s2, e2);
+    two_sum(s2, -w_hi, s3, e3);
+    return __fadd_rn(s3, __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), e3),
+                                   __fadd_rn(__fadd_rn(ex, ey), __fsub_rn(ez, w_lo))));
 }
-template <typename R>
-__device__ __forceinline__ R sphere_in(R rr, R b, R rw2) {
-    const R c = rr - rw2;
-    const R disc = b * b - c;
-    if (disc < R(0)) return R(F_INF);
-    const R s = c / (-b + sqrt(disc));
-    return s > R(0) ? s : R(0);
+
+// Roots of s^2 + 2 b s + c = 0 given disc = b^2 - c.
+// Outer sphere: the far root (always ahead of a point inside), without cancellation:
+// -c / (b + sq) when moving outwards, -b + sq otherwise.
+__device__ __forceinline__ float sphere_out_root(float b, float c, float disc) {
+    const float sq = sqrtf(fmaxf(disc, 0.f));
+    const float s = b > 0.f ? -c / (b + sq) : -b + sq;
+    return fmaxf(s, 0.f);
+}
+// Inner sphere: the near root, only while moving inwards (b < 0).
+__device__ __forceinline__ float sphere_in_root(float b, float c, float disc) {
+    if (disc < 0.f) return F_INF;
+    return fmaxf(c / (-b + sqrtf(disc)), 0.f);
+}
+
+// FP64 p.u and |p|^2 from FP32 inputs.
+struct SphQ64 { double b, rr; };
+__device__ __forceinline__ SphQ64 sphere_terms64(const Ray& r) {
+    const double px = r.p.x, py = r.p.y, pz = r.p.z;
+    SphQ64 q;
+    q.rr = fma(px, px, fma(py, py, pz * pz));
+    q.b = fma(px, (double)r.u.x, fma(py, (double)r.u.y, pz * (double)r.u.z));
+    return q;
+}
+
+// Cone coefficients: the ray meets z sin(w) = R cos(w) (both nappes) where
+// A s^2 + 2 B s + C = 0; disc = B^2 - A C.
+struct ConeQ { float A, B, C, disc; };
+
+// FP32: uR2 = u_x^2 + u_y^2, pu = p_x u_x + p_y u_y and Rp = |p_R| are shared by both cones;
+// C = f (p_z sin + Rp cos) with f = p_z sin - Rp cos = r sin(theta_w - theta) formed directly.
+__device__ __forceinline__ ConeQ cone_coeffs32(const Ray& r, float uR2, float pu, float Rp, float cw, float sw) {
+    const float sw2 = sw * sw, cw2 = cw * cw;
+    ConeQ q;
+    q.A = r.u.z * r.u.z * sw2 - uR2 * cw2;
+    q.B = r.p.z * r.u.z * sw2 - pu * cw2;
+    const float f = r.p.z * sw - Rp * cw;
+    q.C = f * (r.p.z * sw + Rp * cw);
+    q.disc = q.B * q.B - q.A * q.C;
+    return q;
+}
+
+// FP64 coefficients from the FP32 ray (exact products, rounded sums), rounded to FP32.  Out of
+// line with scalar arguments: the call is rare, and an inlined FP64 block would be scheduled
+// (and its operands converted) on the common path.
+static __device__ __noinline__ ConeQ cone_coeffs64(float px_, float py_, float pz_, float ux_, float uy_, float uz_,
+                                                  double cw, double sw) {
+    const double px = px_, py = py_, pz = pz_, ux = ux_, uy = uy_, uz = uz_;
+    const double sw2 = sw * sw, cw2 = cw * cw;
+    const double uR2 = fma(ux, ux, uy * uy), pu = fma(px, ux, py * uy), R2 = fma(px, px, py * py);
+    const double A = fma(uz * uz, sw2, -uR2 * cw2);
+    const double B = fma(pz * uz, sw2, -pu * cw2);
+    const double C = fma(pz * pz, sw2, -R2 * cw2);
+    ConeQ q;
+    q.A = (float)A; q.B = (float)B; q.C = (float)C;
+    q.disc = (float)fma(B, B, -A * C);
+    return q;
+}
+
+// The smallest root >= -tol on the cone's own nappe through which the ray leaves the cell in
+// the given sense (+1: theta decreasing, f increasing), or +inf.
+__device__ __forceinline__ float cone_pick(const ConeQ& q, const Ray& r, float cw, float sw, int sense, float tol) {
+    if (q.disc < 0.f) return F_INF;
+    const float sq = sqrtf(q.disc);
+    const float qq = -(q.B + copysignf(sq, q.B));
+    float roots[2];
+    roots[0] = (q.A != 0.f) ? qq / q.A : F_INF;
+    roots[1] = (qq != 0.f) ? q.C / qq : F_INF;
+    float best = F_INF;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float s = roots[t];
+        if (!(s >= -tol) || !(s < best)) continue;
+        const float qz = r.p.z + s * r.u.z;
+        if (!(qz * cw > 0.f)) continue;        // other nappe
+        const float qx = r.p.x + s * r.u.x, qy = r.p.y + s * r.u.y;
+        const float Rq2 = qx * qx + qy * qy;
+        if (Rq2 == 0.f) continue;
+        // sign of df/ds = u_z sin - cos (q_R . u_R) / |q_R|, scaled by |q_R| > 0 (no division)
+        const float dfds = r.u.z * sw * sqrtf(Rq2) - cw * (qx * r.u.x + qy * r.u.y);
+        if (sense > 0 ? !(dfds > 0.f) : !(dfds < 0.f)) continue;
+        best = fmaxf(s, 0.f);
+    }
+    return best;
 }
 
 __device__ __forceinline__ float phi_root(const Ray& r, float cw, float sw, int sense, float tol) {
@@ -171,17 +228,32 @@ __device__ __forceinline__ float phi_root(const Ray& r, float cw, float sw, int 
     return fmaxf(s, 0.f);
 }
 
-// Exit through cone wall jw in the given sense; FP64 for walls near the polar axis.
+// Exit through cone wall jw in the given sense (the midplane wall is the plane z = 0); `best`
+// is the nearest exit found so far.
 __device__ __forceinline__ float cone_wall(const DevGrid& g, const Ray& r, int jw, int sense, float uR2, float pu,
-                                          float Rp, float tol) {
-    const float sw = __ldg(g.sth + jw);
-    if (sw < g.sin_fp64) {
-        const double px = r.p.x, py = r.p.y, ux = r.u.x, uy = r.u.y;
-        return (float)cone_root<double>(px, py, r.p.z, ux, uy, r.u.z, ux * ux + uy * uy, px * ux + py * uy,
-                                        sqrt(px * px + py * py), __ldg(g.cthd + jw), __ldg(g.sthd + jw), sense,
-                                        (double)tol);
+                                          float Rp, float tol, float best) {
+    const float cw = __ldg(g.cth + jw), sw = __ldg(g.sth + jw);
+    if (cw == 0.f) {           // f = z increases when u_z > 0
+        if (r.u.z == 0.f || ((sense > 0) != (r.u.z > 0.f))) return F_INF;
+        const float s = -r.p.z / r.u.z;
+        return s < -tol ? F_INF : fmaxf(s, 0.f);
     }
-    return cone_root<float>(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, uR2, pu, Rp, __ldg(g.cth + jw), sw, sense, tol);
+    ConeQ q;
+    bool fp64 = sw < g.sin_fp64;
+    if (!fp64) {
+        q = cone_coeffs32(r, uR2, pu, Rp, cw, sw);
+        // Grazing: both roots lie within 3.2% of s_c = -B/A (|disc| < 2^-10 B^2 plus its FP32
+        // rounding error ~2^-21 B^2 leave sqrt(|disc|) < 0.032 |B|), so the root nearest zero is
+        // no closer than 0.96 s_c.  The FP64 redo is needed only where a root can be the exit,
+        // not behind the ray and not beyond `best`: a ray running along a cone far from its
+        // tangent point stays "grazing" for many steps while that cone is never its exit.
+        if (fabsf(q.disc) < 0x1p-10f * q.B * q.B) {
+            const float s0 = 0.96f * (-q.B / q.A);
+            fp64 = s0 >= -tol && s0 < best;
+        }
+    }
+    if (fp64) q = cone_coeffs64(r.p.x, r.p.y, r.p.z, r.u.x, r.u.y, r.u.z, __ldg(g.cthd + jw), __ldg(g.sthd + jw));
+    return cone_pick(q, r, cw, sw, sense, tol);
 }
 
 // Distance to the exit of the current cell; axis 0/1/2 = r/theta/phi, dir = +-1.
@@ -189,28 +261,40 @@ __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& a
     const float rr = dot3(r.p, r.p);
     const float b = dot3(r.p, r.u);
     const float tol = 2e-6f * sqrtf(rr) + 1e-30f;
-    float best;
-    const float rout = __ldg(g.rw + r.i + 1);
     // A ray enters the inner sphere only when clearly moving inwards: a ray tangent to the
     // sphere touches it at one point, and FP32 rounding of p.u around zero must not make it
     // cross back and forth there.
     const float b_in = -1e-6f * sqrtf(rr);
-    if (rout < g.r_fp64) {
-        const double pd[3] = {r.p.x, r.p.y, r.p.z}, ud[3] = {r.u.x, r.u.y, r.u.z};
-        const double rrd = pd[0] * pd[0] + pd[1] * pd[1] + pd[2] * pd[2];
-        const double bd = pd[0] * ud[0] + pd[1] * ud[1] + pd[2] * ud[2];
-        const double ro = __ldg(g.rwd + r.i + 1), ri = __ldg(g.rwd + r.i);
-        best = (float)sphere_out<double>(rrd, bd, ro * ro);
-        axis = 0; dir = 1;
-        if (ri > 0.0 && bd < (double)b_in) {
-            const float s = (float)sphere_in<double>(rrd, bd, ri * ri);
+    const bool inward = b < b_in && __ldg(g.rw + r.i) > 0.f;
+    float best;
+    axis = 0; dir = 1;
+    if (__ldg(g.rw + r.i + 1) < g.r_fp64) {
+        const SphQ64 t = sphere_terms64(r);
+        const double ro = __ldg(g.rwd + r.i + 1);
+        const double co = fma(-ro, ro, t.rr);
+        const float bf = (float)t.b;
+        best = sphere_out_root(bf, (float)co, (float)fma(t.b, t.b, -co));
+        if (inward) {
+            const double ri = __ldg(g.rwd + r.i);
+            const double ci = fma(-ri, ri, t.rr);
+            const float s = sphere_in_root(bf, (float)ci, (float)fma(t.b, t.b, -ci));
             if (s < best) { best = s; dir = -1; }
         }
     } else {
-        best = sphere_out<float>(rr, b, __ldg(g.r2w + r.i + 1));
-        axis = 0; dir = 1;
-        if (b < b_in && __ldg(g.rw + r.i) > 0.f) {
-            const float s = sphere_in<float>(rr, b, __ldg(g.r2w + r.i));
+        const float co = sphere_c(r.p, __ldg(g.r2w + r.i + 1), __ldg(g.r2wl + r.i + 1));
+        best = sphere_out_root(b, co, fmaf(b, b, -co));
+        if (inward) {
+            const float ci = sphere_c(r.p, __ldg(g.r2w + r.i), __ldg(g.r2wl + r.i));
+            float disc = fmaf(b, b, -ci);
+            float bb = b;
+            if (fabsf(disc) < 0x1p-10f * b * b) {           // grazing the inner sphere
+                const SphQ64 t = sphere_terms64(r);
+                const double ri = __ldg(g.rwd + r.i);
+                const double ci64 = fma(-ri, ri, t.rr);
+                disc = (float)fma(t.b, t.b, -ci64);
+                bb = (float)t.b;
+            }
+            const float s = sphere_in_root(bb, ci, disc);
             if (s < best) { best = s; dir = -1; }
         }
     }
@@ -220,11 +304,11 @@ __device__ __forceinline__ float sph_exit(const DevGrid& g, const Ray& r, int& a
     const float Rp = sqrtf(r.p.x * r.p.x + r.p.y * r.p.y);
     // lower wall j is left with theta decreasing (sense +1), upper wall j + 1 increasing (-1)
     if (r.j > 0) {
-        const float s = cone_wall(g, r, r.j, +1, uR2, pu, Rp, tol);
+        const float s = cone_wall(g, r, r.j, +1, uR2, pu, Rp, tol, best);
         if (s < best) { best = s; axis = 1; dir = -1; }
     }
     if (r.j + 1 < g.n2) {
-        const float s = cone_wall(g, r, r.j + 1, -1, uR2, pu, Rp, tol);
+        const float s = cone_wall(g, r, r.j + 1, -1, uR2, pu, Rp, tol, best);
         if (s < best) { best = s; axis = 1; dir = 1; }
     }
     if (g.n3 > 1) {

@@ -38,14 +38,14 @@ __device__ __forceinline__ void flush_deposit(double* acc, bool flushing, int32_
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         if (!flushing) return;
         if (__popc(peers) == 1) {
-            atomicAdd(acc + ci, (double)v);
+            atomicAdd(acc + ci, widen(v));
             return;
         }
         float sum = 0.f;
         for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
-        if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(acc + ci, (double)sum);
+        if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(acc + ci, widen(sum));
     } else {
-        if (flushing) atomicAdd(acc + ci, (double)v);
+        if (flushing) atomicAdd(acc + ci, widen(v));
     }
 }
 
@@ -120,12 +120,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
             r[13] = pk.nu; r[14] = (float)pobs; r[15] = (float)where;
         }
-        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
         dep_ci = -1;
         mode = M_DONE;
     };
     auto end_packet = [&]() {
-        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
         dep_ci = -1;
         dep_val = 0.f;
         lc.v[C_PACKETS_DONE]++;
@@ -288,7 +288,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         }
         if (((++rounds) & 255u) == 0) watchdog(rounds);
     }
-    if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, (double)dep_val);
+    if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
 }
 
 // ---------------------------------------------------------------- one model

@@ -19,8 +19,9 @@ struct DevGrid {
     const float* w3;
     // spherical: radii (scaled) and squares, polar walls (angle, cos, sin), azimuthal walls
     const float* rw;               // [n1+1]
-    const float* r2w;              // [n1+1]
-    const double* rwd;             // [n1+1] FP64 radii for small-r solves
+    const float* r2w;              // [n1+1] r^2 rounded to FP32
+    const float* r2wl;             // [n1+1] r^2 - r2w (the FP32 pair holds r^2 to ~2^-48)
+    const double* rwd;             // [n1+1] FP64 radii for small-r and grazing solves
     const float* thw;              // [n2+1]
     const float* cth;              // [n2+1] cos, exactly 0 for the midplane wall
     const float* sth;
@@ -30,8 +31,8 @@ struct DevGrid {
     const float* cph;
     const float* sph;
     float r0;                      // inner radius (scaled), 0 without a hole
-    float r_fp64;                  // sphere solves for walls below this radius run in FP64
-    float sin_fp64;                // cone solves for walls with sin(theta) below this run in FP64
+    float r_fp64;                  // sphere coefficients for walls below this radius in FP64
+    float sin_fp64;                // cone coefficients for walls with sin(theta) below this in FP64
     int32_t pad0;
 };
 
@@ -70,6 +71,7 @@ struct DevObs {
     const float* ex;               // [nobs][3]
     const float* ey;               // [nobs][3]
     double sed_a, sed_b;           // SED bin = floor(sed_a - sed_b * ln nu)
+    float sed_af, sed_bf;          // the same coefficients rounded to FP32 (screening pass)
     float img_scale;               // nx / (2 * half extent) in scaled units
     float img_half;                // scaled half extent
     const int32_t* img_bin;        // [nimg] SED bin per image wavelength

@@ -28,7 +28,20 @@ __device__ __forceinline__ void flush_counters(const LocalCounters& lc, unsigned
 }
 
 // SED bin of a frequency: floor(nsed ln(lambda/lambda_min) / ln(lambda_max/lambda_min)), -1 outside.
+// The bin is decided by x = sed_a - sed_b ln nu in FP64.  An FP32 pass screens it first: the
+// rounding of sed_a, sed_b, logf (<= 1 ulp), the product and the difference together stay
+// below 2^-22 (|sed_a| + |sed_b ln nu| + |x|); only when x_f lies within 1e-6 of that sum of
+// an integer (a bin edge, 0 or nsed) does the FP64 value decide, so the result is always the
+// FP64 one while the FP64 pipe is used on a small fraction of frequencies.
 __device__ __forceinline__ int sed_bin(const DevObs& o, float nu) {
+    const float t = o.sed_bf * logf(nu);
+    const float xf = o.sed_af - t;
+    const float guard = 1e-6f * (fabsf(o.sed_af) + fabsf(t) + fabsf(xf));
+    const float fl = floorf(xf);
+    if (xf - fl > guard && fl + 1.f - xf > guard) {
+        if (!(fl >= 0.f) || fl >= (float)o.nsed) return -1;
+        return (int)fl;
+    }
     const double x = o.sed_a - o.sed_b * log((double)nu);
     if (!(x >= 0.0) || x >= (double)o.nsed) return -1;
     return (int)x;

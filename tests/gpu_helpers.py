@@ -58,3 +58,53 @@ def random_points_in_grid(om, n, rng, radius):
         dirs.append(u)
         cells.append(c.copy())
     return np.array(pts), np.array(dirs), np.array(cells, np.int32)
+
+
+def points_in_shell(om, n, rng, r_lo, r_hi, cos_band=None, graze=None):
+    """Points with r log-uniform in [r_lo, r_hi] and, with cos_band = c0, |cos theta| >= c0
+    (the polar regions); directions isotropic, or with graze = g, inclined to the sphere
+    through the point by less than g (|p.u| / |p| < g): rays grazing the spherical walls."""
+    pts, dirs, cells = [], [], []
+    out = np.zeros(3)
+    c = np.zeros(3, np.int32)
+    while len(pts) < n:
+        r = math.exp(rng.uniform(math.log(r_lo), math.log(r_hi)))
+        if cos_band is None:
+            mu = rng.uniform(-1.0, 1.0)
+        else:
+            mu = math.copysign(rng.uniform(cos_band, 1.0), rng.uniform(-1.0, 1.0))
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        st = math.sqrt(max(0.0, 1.0 - mu * mu))
+        rhat = np.array([st * math.cos(ph), st * math.sin(ph), mu])
+        p = r * rhat
+        if graze is None:
+            u = rng.normal(size=3)
+        else:
+            t = rng.normal(size=3)
+            t -= (t @ rhat) * rhat
+            t /= np.linalg.norm(t)
+            u = t + rng.uniform(-graze, graze) * rhat
+        u /= np.linalg.norm(u)
+        s = M.lib().or_locate(om._struct, M._ptr(p), M._ptr(u), M._ptr(out), M._ptr(c, M._ip))
+        if s != 0 or not np.allclose(out, p):
+            continue
+        pts.append(p.copy())
+        dirs.append(u)
+        cells.append(c.copy())
+    return np.array(pts), np.array(dirs), np.array(cells, np.int32)
+
+
+def grid_scale(wl):
+    """L0, the unit the library scales lengths by: the largest |wall| of a Cartesian grid, the
+    outer radius of a spherical one."""
+    axes = range(3) if wl.grid_type == "cartesian" else range(1)
+    return max(max(abs(float(wl.walls[a][0])), abs(float(wl.walls[a][-1]))) for a in axes)
+
+
+def as_device_sees(p, wl):
+    """(FP32 positions in cm handed to the step hooks, FP64 positions in cm the oracle gets):
+    the hooks scale by an FP32 1/L0, so the oracle is given that rounded position times L0."""
+    L0 = grid_scale(wl)
+    p32 = np.asarray(p, np.float64).astype(np.float32)
+    seen = p32 * np.float32(1.0 / L0)          # FP32 product, rounded like the device's
+    return p32, seen.astype(np.float64) * L0

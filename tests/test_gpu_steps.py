@@ -11,7 +11,8 @@ from oracle import mc as M
 from oracle import tables as T
 from paper_1112_1071_gb300 import hrt
 from paper_1112_1071_gb300 import workloads as W
-from tests.gpu_helpers import dev, random_points_in_grid, spherical_test_grid, torch_cuda, workload_from_walls
+from tests.gpu_helpers import (as_device_sees, dev, points_in_shell, random_points_in_grid, spherical_test_grid,
+                               torch_cuda, workload_from_walls)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,8 +35,12 @@ def test_philox_words_bit_exact():
         assert list(got[i]) == M.philox4x32_10(ctr[i], key[i])
 
 
-@pytest.mark.parametrize("kind", ["cartesian", "spherical_hole_phi", "spherical_disk"])
+@pytest.mark.parametrize("kind", ["cartesian", "spherical_hole_phi", "spherical_disk", "disk_inner_rim",
+                                  "disk_polar", "disk_grazing"])
 def test_cell_exit_matches_oracle(kind):
+    """Random rays; the disk cases also sample the regions where the FP32 solves are most
+    exposed: the first shells outside the inner hole, the polar cones, and rays inclined by
+    less than 2 % to the spheres (grazing the inner sphere and the cones)."""
     torch = torch_cuda()
     rng = np.random.default_rng(1)
     if kind == "cartesian":
@@ -49,9 +54,18 @@ def test_cell_exit_matches_oracle(kind):
         radius = 990 * W.AU
     om = M.OracleModel(wl)
     om.struct(np.zeros(om.nc, np.int32))
-    p, u, c = random_points_in_grid(om, 4000, rng, radius)
-    # both sides see the same (FP32-representable) inputs
-    p = p.astype(np.float32).astype(np.float64)
+    r_in = wl.walls[0][0]
+    if kind == "disk_inner_rim":
+        p, u, c = points_in_shell(om, 4000, rng, r_in, 1.5 * r_in)
+    elif kind == "disk_polar":
+        p, u, c = points_in_shell(om, 4000, rng, r_in, 0.99 * wl.walls[0][-1], cos_band=math.cos(0.15))
+    elif kind == "disk_grazing":
+        p, u, c = points_in_shell(om, 4000, rng, r_in, 0.99 * wl.walls[0][-1], graze=0.02)
+    else:
+        p, u, c = random_points_in_grid(om, 4000, rng, radius)
+    # both sides see the same inputs: FP32 directions, and the scaled FP32 position the device
+    # computes from the FP32 cm position it is given
+    p32, p = as_device_sees(p, wl)
     u = u.astype(np.float32).astype(np.float64)
     want = np.empty(len(p))
     want_ax = np.empty(len(p), np.int32)
@@ -64,7 +78,7 @@ def test_cell_exit_matches_oracle(kind):
     m = hrt.Model(wl)
     dist = torch.empty(len(p), dtype=torch.float32, device="cuda")
     ex = torch.empty(len(p), dtype=torch.int32, device="cuda")
-    pd, ud, cd = dev(p.astype(np.float32)), dev(u.astype(np.float32)), dev(c)
+    pd, ud, cd = dev(p32), dev(u.astype(np.float32)), dev(c)
     m.step("hrt_step_cell_exit", len(p), pd.data_ptr(), ud.data_ptr(), cd.data_ptr(), dist.data_ptr(), ex.data_ptr())
     got = dist.cpu().numpy().astype(np.float64)
     gax = ex.cpu().numpy()
@@ -94,7 +108,7 @@ def test_tau_to_edge_matches_oracle(kind):
     om = M.OracleModel(wl)
     om.struct(np.zeros(om.nc, np.int32))
     p, u, _ = random_points_in_grid(om, 3000, rng, radius)
-    p = p.astype(np.float32).astype(np.float64)
+    p32, p = as_device_sees(p, wl)
     u = u.astype(np.float32).astype(np.float64)
     nus = np.exp(rng.uniform(np.log(wl.nu[0]), np.log(wl.nu[-1]), len(p))).astype(np.float32).astype(np.float64)
     want = np.empty(len(p))
@@ -103,7 +117,7 @@ def test_tau_to_edge_matches_oracle(kind):
         want[q] = M.lib().or_tau_to_edge(om._struct, M._ptr(p[q]), M._ptr(u[q]), chi)
     m = hrt.Model(wl)
     tau = torch.empty(len(p), dtype=torch.float32, device="cuda")
-    pd, ud, nd = dev(p.astype(np.float32)), dev(u.astype(np.float32)), dev(nus.astype(np.float32))
+    pd, ud, nd = dev(p32), dev(u.astype(np.float32)), dev(nus.astype(np.float32))
     m.step("hrt_step_tau_to_edge", len(p), pd.data_ptr(), ud.data_ptr(), nd.data_ptr(), tau.data_ptr())
     got = tau.cpu().numpy().astype(np.float64)
     tol = 2e-5 * np.abs(want) + 1e-6
