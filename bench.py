@@ -72,6 +72,19 @@ def config(args, world):
             "kernel": args.kernel}
 
 
+def job_throughput(total_ms, e2e_ms, world, packets_step, steps, dist=None, device="cpu"):
+    """Whole-job packets/s over `world` ranks that each ran `steps` timed steps of
+    `packets_step` packets: the slowest rank's timed total and mean end-to-end step (max over
+    ranks) set the time.  Returns (value, e2e value, total_ms, e2e_ms) after the reduction."""
+    if dist is not None:
+        import torch
+        tt = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(tt[0]), float(tt[1])
+    value = world * packets_step * steps / (total_ms * 1e-3)
+    return value, world * packets_step / (e2e_ms * 1e-3), total_ms, e2e_ms
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -259,15 +272,8 @@ def main():
 
     packets_step = args.packets * (args.iters + 1)
     ms = statistics.mean(step_ms)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        tt = torch.tensor([total_ms, statistics.mean(e2e_ms)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, e2e_mean = float(tt[0]), float(tt[1])
-    else:
-        e2e_mean = statistics.mean(e2e_ms)
-    value = world * packets_step * args.steps / (total_ms * 1e-3)
-    e2e_value = world * packets_step / (e2e_mean * 1e-3)
+    value, e2e_value, _, _ = job_throughput(sum(step_ms), statistics.mean(e2e_ms), world, packets_step, args.steps,
+                                            dist, "cuda")
 
     # ---- roofline of the propagation kernel (Lucy iterations and the peel-off pass)
     last = all_stats[-1]

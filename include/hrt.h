@@ -132,6 +132,14 @@ typedef struct {
                                     than this are still walking (1..32, 0 = tuned default) */
     double watchdog_ms;          /* > 0: the propagation kernel stops after this long and the call
                                     returns HRT_ETIMEDOUT (the context stays usable) */
+    int64_t first_packet;        /* the call runs packet ids first_packet .. first_packet + n_packets - 1
+                                    of the iteration (each id has its own Philox stream); default 0 */
+    int64_t n_total;             /* packets of the whole iteration, eps = L_total dt / n_total; 0 (default)
+                                    = n_packets.  With n_total > n_packets the call runs one share of an
+                                    iteration (Sect. 3: packet chunks are independent and their
+                                    accumulators add): a shard of a partitioned run, or a sample that
+                                    can be checked packet by packet.  Needs first_packet >= 0 and
+                                    first_packet + n_packets <= n_total <= 2^32 (else HRT_EINVAL). */
 } hrt_run_params;
 
 typedef struct {

@@ -237,6 +237,7 @@ int stage_sources(hrt_ctx* ctx) {
     S.npoint = npt; S.nsrc = nsrc; S.nspec = NSPEC;
     S.pos = ctx->d_src_pos.p; S.cdf = ctx->d_src_cdf.p; S.spec_nu = ctx->d_spec_nu.p; S.spec_cdf = ctx->d_spec_cdf.p;
     S.cell_cdf = cell ? ctx->d_cell_cdf.p : nullptr;
+    S.col = nullptr;            // set per imaging pass
     ctx->dirty_src = false;
     return HRT_OK;
 }
@@ -340,10 +341,11 @@ int hrt_destroy(hrt_ctx* ctx) {
     if (!ctx) return HRT_EINVAL;
     DeviceGuard dg(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto* b : {&ctx->d_rhoL, &ctx->d_w1, &ctx->d_w2, &ctx->d_w3, &ctx->d_rw, &ctx->d_r2w, &ctx->d_r2wl, &ctx->d_thw, &ctx->d_cth,
-                    &ctx->d_sth, &ctx->d_phw, &ctx->d_cph, &ctx->d_sph, &ctx->d_lnu, &ctx->d_inv_dlnu, &ctx->d_lchi,
-                    &ctx->d_alb, &ctx->d_nuf, &ctx->d_cdf_emit, &ctx->d_src_pos, &ctx->d_spec_nu, &ctx->d_spec_cdf,
-                    &ctx->d_obs_n, &ctx->d_obs_ex, &ctx->d_obs_ey})
+    for (auto* b : {&ctx->d_rhoL, &ctx->d_w1, &ctx->d_w2, &ctx->d_w3, &ctx->d_rw, &ctx->d_r2w, &ctx->d_r2wl,
+                    &ctx->d_thw, &ctx->d_cth, &ctx->d_sth, &ctx->d_phw, &ctx->d_cph, &ctx->d_sph, &ctx->d_lnu,
+                    &ctx->d_inv_dlnu, &ctx->d_lchi, &ctx->d_alb, &ctx->d_nuf, &ctx->d_cdf_emit, &ctx->d_src_pos,
+                    &ctx->d_spec_nu, &ctx->d_spec_cdf, &ctx->d_obs_n, &ctx->d_obs_ex, &ctx->d_obs_ey,
+                    &ctx->d_src_col})
         b->release();
     for (auto* b : {&ctx->d_rwd, &ctx->d_cthd, &ctx->d_sthd, &ctx->d_va, &ctx->d_vb, &ctx->d_vc, &ctx->d_nu,
                     &ctx->d_kappa, &ctx->d_Tn, &ctx->d_lnT, &ctx->d_E, &ctx->d_lnE, &ctx->d_src_cdf, &ctx->d_cell_cdf,
@@ -558,6 +560,9 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (n_packets < 1 || n_packets > 0xFFFFFFFFll) return ctx->fail(HRT_EINVAL, "n_packets must be in [1, 2^32)");
     if (!(P.p > 0 && P.p <= 1)) return ctx->fail(HRT_EINVAL, "percentile p must be in (0, 1]");
     if (P.max_interactions < 0) return ctx->fail(HRT_EINVAL, "max_interactions < 0");
+    const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
+    if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
+        return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");
     DeviceGuard dg(ctx->device);
     int rc = prepare(ctx);
     if (rc != HRT_OK) return rc;
@@ -597,12 +602,12 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     RunArgs& A = job.args;
     A = RunArgs{};
     A.n_packets = n_packets;
-    A.first_packet = 0;
+    A.first_packet = P.first_packet;
     A.key0 = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
     A.key1 = (uint32_t)(ctx->seed >> 32);
     A.iter_key = P.update_temperature ? (uint32_t)ctx->iteration : (0x80000000u | (uint32_t)ctx->iteration);
     A.model_key = ctx->model_id;
-    A.eps = ctx->L_tot / (double)n_packets;
+    A.eps = ctx->L_tot / (double)n_total;
     ctx->last_eps = A.eps;
     A.epsL0 = A.eps * ctx->L0;
     A.max_interactions = P.max_interactions;
@@ -623,7 +628,15 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     }
     CK(launch_stamp(ctx->d_work.p + 1, s), "stamp");
     launched++;
+    const bool columns = A.peel && ctx->src.npoint > 0;
+    if (columns) CK(ctx->d_src_col.alloc((size_t)ctx->src.npoint * ctx->obs.nobs), "source columns");
     CK(cudaEventRecord(ctx->ev[3], s), "event");
+    job.src.col = nullptr;
+    if (columns) {
+        CK(launch_source_columns(job.grid, job.src, job.obs, ctx->d_src_col.p, s), "source columns");
+        job.src.col = ctx->d_src_col.p;
+        launched++;
+    }
     cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
                                                  : launch_propagate_event(job, L, s, &launched);
     CK(e, "propagate");
@@ -666,7 +679,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     std::memset(&st, 0, sizeof(st));
     st.iteration = ctx->iteration;
     st.n_packets = n_packets;
-    st.e_emitted = ctx->L_tot;
+    st.e_emitted = n_total == n_packets ? ctx->L_tot : A.eps * (double)n_packets;
     st.e_escaped = (double)h[C_ESCAPED] * A.eps;
     st.e_killed = (double)h[C_KILLED] * A.eps;
     st.e_absorbed = (double)h[C_ABSORBED_TERM] * A.eps;

@@ -94,7 +94,7 @@ struct hrt_ctx {
     DBuf<float> d_src_pos, d_spec_nu, d_spec_cdf;
     DBuf<double> d_src_cdf, d_cell_cdf, d_spec_nud, d_teff, d_unu, d_uf;
     DBuf<int> d_uoff, d_un;
-    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey;
+    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey, d_src_col;
     DBuf<int32_t> d_img_bin;
     // ---- device state
     DBuf<double> d_T, d_adot, d_acc, d_sed, d_img;

@@ -78,8 +78,14 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         zero_run = 0;
         mode = M_WALK;
     };
-    // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction)
+    // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction);
+    // emission from a point source with precomputed columns needs no walk
     auto start_peel = [&](int ob) {
+        if (prelocate && s.col) {
+            tau = pk.dust.chi * __ldg(s.col + (int64_t)pk.src * o.nobs + ob);
+            mode = M_PEEL_DONE;
+            return;
+        }
         pk.r = saved;
         pk.r.p = porg;
         set_dir(pk.r, make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2)));
@@ -171,27 +177,29 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 }
             }
         } else if (mode == M_PEEL_DONE) {
-            const float3 n = pk.r.u;
-            const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
-            const double w = a.eps * (double)(prob * expf(-tau));
-            if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
-            else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
-            if (o.nimg > 0) {
-                const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
-                const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
-                const int ix = (int)floorf((px + o.img_half) * o.img_scale);
-                const int iy = (int)floorf((py + o.img_half) * o.img_scale);
-                if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
-                    for (int l = 0; l < o.nimg; ++l)
-                        if (__ldg(o.img_bin + l) == pk.sbin)
-                            atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
-            }
-            if (++pobs < o.nobs) {
-                start_peel(pobs);
-            } else {
-                pk.r = saved;
-                start_walk();
-            }
+            do {   // peel rays that need no walk (precomputed columns, start outside) end here
+                const float3 n = make_float3(__ldg(o.n + 3 * pobs), __ldg(o.n + 3 * pobs + 1), __ldg(o.n + 3 * pobs + 2));
+                const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
+                const double w = a.eps * (double)(prob * expf(-tau));
+                if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
+                else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
+                if (o.nimg > 0) {
+                    const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
+                    const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
+                    const int ix = (int)floorf((px + o.img_half) * o.img_scale);
+                    const int iy = (int)floorf((py + o.img_half) * o.img_scale);
+                    if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
+                        for (int l = 0; l < o.nimg; ++l)
+                            if (__ldg(o.img_bin + l) == pk.sbin)
+                                atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
+                }
+                if (++pobs < o.nobs) {
+                    start_peel(pobs);
+                } else {
+                    pk.r = saved;
+                    start_walk();
+                }
+            } while (mode == M_PEEL_DONE);
         }
         // refill: lanes without a packet take the next ids
         const unsigned need = __ballot_sync(FULL, mode == M_NEED);

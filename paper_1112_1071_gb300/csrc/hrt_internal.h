@@ -31,6 +31,8 @@ struct PropagateJob {
 // propagate.cu
 cudaError_t launch_stamp(unsigned long long* t0, cudaStream_t s);
 cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
+cudaError_t launch_source_columns(const DevGrid& g, const DevSources& src, const DevObs& o, float* col,
+                                  cudaStream_t s);
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
 
 // event.cu: one persistent launch over the (model, packet range) chunks of grid type gtype

@@ -60,6 +60,8 @@ struct DevSources {
     const float* spec_nu;          // [nspec]
     const float* spec_cdf;         // [nsrc][nspec]
     const double* cell_cdf;        // [ncells] cumulative cell luminosity or null
+    const float* col;              // [npoint][nobs] sum of rhoL l from each point source along each
+                                   // observer direction (imaging passes), or null
 };
 
 struct DevObs {

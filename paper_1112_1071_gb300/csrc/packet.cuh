@@ -56,6 +56,7 @@ struct Packet {
     PacketRng rng;
     float3 last_origin;      // emission position (before any hole crossing)
     int32_t emit_relocate;   // 1: emission peel rays must locate their cell along the observer
+    int32_t src;             // emitting source
 };
 
 __device__ __forceinline__ void set_frequency(Packet& pk, const DevDust& d, const DevObs& o, float nu) {
@@ -69,10 +70,12 @@ enum PeelKind : int32_t { PEEL_ISO = 0, PEEL_HG = 1 };
 // Peel-off towards every observer from position r.p: weight eps p exp(-tau_obs).  With
 // relocate, the starting cell is found along each observer direction (emission from a point
 // source, which may sit on walls or in the spherical hole); otherwise the packet's cell is used.
+// With col (emission from a point source whose columns were precomputed), tau_obs = chi col[ob]:
+// every packet of that source peels along the same rays, so they are walked once per pass.
 template <int G>
 __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, const RunArgs& a,
                            const Tallies& t, double* sed_s, const Ray& at, float3 uin, int kind, bool relocate,
-                           float chi, int sbin, LocalCounters& lc) {
+                           float chi, int sbin, LocalCounters& lc, const float* col = nullptr) {
     if (sbin < 0) return;
     for (int ob = 0; ob < o.nobs; ++ob) {
         const float3 n = make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2));
@@ -81,8 +84,11 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
         set_dir(pr, n);
         float tau = 0.f;
         bool inside = true;
-        if (relocate) inside = grid_locate<G>(g, pr);
-        if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], F_INF);
+        if (col) tau = chi * __ldg(col + ob);
+        else {
+            if (relocate) inside = grid_locate<G>(g, pr);
+            if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], F_INF);
+        }
         const double w = a.eps * (double)(prob * expf(-tau));
         if (sed_s) atomicAdd(sed_s + ob * o.nsed + sbin, w);
         else atomicAdd(t.sed + (int64_t)ob * o.nsed + sbin, w);
@@ -110,6 +116,7 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
     pk.rng.init(make_uint2(a.key0, a.key1), (uint32_t)pid, a.iter_key, a.model_key);
     pk.nint = 0;
     const int src = (int)select_cdf<double>(s.cdf, s.nsrc, (double)pk.rng.next());
+    pk.src = src;
     if (src < s.npoint) {
         pk.r.p = make_float3(__ldg(s.pos + 3 * src), __ldg(s.pos + 3 * src + 1), __ldg(s.pos + 3 * src + 2));
         const float u1 = pk.rng.next(), u2 = pk.rng.next();
@@ -119,7 +126,9 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
         pk.last_origin = at.p;
         pk.emit_relocate = 1;
         if (!grid_locate<G>(g, pk.r)) return false;
-        if (a.peel && inline_peel) peel_event<G>(g, d, o, a, t, sed_s, at, pk.r.u, PEEL_ISO, true, pk.dust.chi, pk.sbin, lc);
+        if (a.peel && inline_peel)
+            peel_event<G>(g, d, o, a, t, sed_s, at, pk.r.u, PEEL_ISO, true, pk.dust.chi, pk.sbin, lc,
+                          s.col ? s.col + (int64_t)src * o.nobs : nullptr);
     } else {
         pk.emit_relocate = 0;
         const int64_t c = select_cdf<double>(s.cell_cdf, g.ncells, (double)pk.rng.next());

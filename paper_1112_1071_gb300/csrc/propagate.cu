@@ -97,6 +97,33 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
     flush_shared(o, a, t, st);
 }
 
+// Columns sum rhoL l from each point source to the grid edge along each observer direction: the
+// peel-off rays of every packet emitted by a point source start at the source and run along the
+// observer direction, so their optical depth is chi(nu) times this column (Sect. 2.6.2).
+template <int G>
+__global__ void k_source_columns(DevGrid g, DevSources s, DevObs o, float* col) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.npoint * o.nobs) return;
+    const int src = q / o.nobs, ob = q % o.nobs;
+    Ray r;
+    r.p = make_float3(s.pos[3 * src], s.pos[3 * src + 1], s.pos[3 * src + 2]);
+    set_dir(r, make_float3(o.n[3 * ob], o.n[3 * ob + 1], o.n[3 * ob + 2]));
+    float sum = 0.f;
+    unsigned long long ncross = 0;
+    if (grid_locate<G>(g, r)) sum = tau_to_edge<G>(g, r, 1.f, ncross, F_INF);
+    col[q] = sum;
+}
+
+cudaError_t launch_source_columns(const DevGrid& g, const DevSources& src, const DevObs& o, float* col,
+                                  cudaStream_t s) {
+    const int n = src.npoint * o.nobs;
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 127) / 128;
+    if (g.type == GRID_CARTESIAN) k_source_columns<GRID_CARTESIAN><<<blocks, 128, 0, s>>>(g, src, o, col);
+    else k_source_columns<GRID_SPHERICAL><<<blocks, 128, 0, s>>>(g, src, o, col);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched) {
     if (job.args.n_packets <= 0) return cudaSuccess;
     Launch ll = l;

@@ -37,7 +37,7 @@ class hrt_run_params(C.Structure):
         ("terminate_on_absorb", C.c_int32), ("quantity", C.c_int32), ("p", C.c_double),
         ("q_thres", C.c_double), ("delta_thres", C.c_double), ("kernel", C.c_int32),
         ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("regroup_threshold", C.c_int32),
-        ("watchdog_ms", C.c_double),
+        ("watchdog_ms", C.c_double), ("first_packet", C.c_int64), ("n_total", C.c_int64),
     ]
 
 

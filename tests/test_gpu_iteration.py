@@ -181,6 +181,10 @@ def test_input_validation_errors():
     assert "outside" in L.hrt_last_error(m.ctx).decode()
     out = np.empty(3)
     assert L.hrt_get_temperature(m.ctx, out.ctypes.data, 3) == hrt.HRT_EINVAL
+    # packet shares beyond the iteration's packet range
+    for kw in (dict(first_packet=900, n_total=1000), dict(first_packet=-1), dict(n_total=2**32 + 1)):
+        with pytest.raises(hrt.HrtError):
+            m.run_iteration(n_packets=200, **kw)
     # the context still runs after rejected calls
     st = m.run_iteration(n_packets=1000)
     assert st["n_packets"] == 1000
