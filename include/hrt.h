@@ -140,6 +140,11 @@ typedef struct {
                                     accumulators add): a shard of a partitioned run, or a sample that
                                     can be checked packet by packet.  Needs first_packet >= 0 and
                                     first_packet + n_packets <= n_total <= 2^32 (else HRT_EINVAL). */
+    int64_t pda_min_visits;      /* partial diffusion approximation (App. A), spherical-polar grids, Lucy
+                                    iterations: cells with dust entered by fewer than this many packets
+                                    (a packet's consecutive path segments in a cell count once) take T
+                                    from the discrete diffusion equation of App. A, with well-sampled
+                                    neighbours as boundary values; 0 (default) = off; < 2^32 */
 } hrt_run_params;
 
 typedef struct {
@@ -156,6 +161,9 @@ typedef struct {
     double ms_propagate;         /* device time of the propagation kernel */
     double ms_total;             /* device time of the whole call */
     int64_t kernel_launches;     /* kernels the call launched */
+    int64_t n_pda;               /* cells whose T came from the diffusion approximation */
+    int64_t pda_iterations;      /* conjugate-gradient iterations of its solve */
+    double pda_residual;         /* |b - A x| / |b| at the end of the solve */
 } hrt_iter_stats;
 
 /* Defaults: max_interactions 1e6, peel 0, update_temperature 1, p 0.99, q_thres 1.02 on T,
@@ -227,6 +235,15 @@ int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* 
 
 /* Tabulated E(T) [nT] and emissivity cdf [nT][nnu] as built on the device (copied to host). */
 int hrt_get_tables(hrt_ctx* ctx, double* E, int64_t nE, float* cdf, int64_t ncdf);
+
+/* Rosseland mean extinction chi_R(T_m) [nT] (cm^2/g) of the dust on the temperature nodes, as
+ * used by the diffusion approximation (App. A): int dB/dT dnu / int chi^-1 dB/dT dnu, trapezoid
+ * rule over the dust nodes.  n >= nT. */
+int hrt_get_rosseland(hrt_ctx* ctx, double* out, int64_t n);
+
+/* Packet entries per cell [cells] counted by the last Lucy iteration that ran with
+ * pda_min_visits > 0 (HRT_ESTATE otherwise).  n must equal the number of cells. */
+int hrt_get_visits(hrt_ctx* ctx, uint32_t* out, int64_t n);
 
 /* ------------------------------------------------------------------ learned warm start
  * Not in the paper: a 3-D convolutional encoder-decoder (U-Net) trained on temperature fields

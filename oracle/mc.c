@@ -143,6 +143,8 @@ typedef struct {
     double* esc;              /* [10][nsed] escape photon binning (cos theta bins x SED bins) */
     double e_escaped, e_killed, e_absorbed;
     int64_t n_interactions, n_scatter, n_absorb, n_crossings, n_peel_crossings, n_killed;
+    int64_t* visits;          /* [Ncells] packet entries (runs of one packet's consecutive deposits in
+                                 the cell): how many packets sampled the cell's estimate (App. A) */
 } or_result;
 
 #define N_ESC_MU 10
@@ -553,8 +555,10 @@ int64_t or_trace(const or_model* m, const double p_in[3], const double u[3], int
 /* ------------------------------------------------------------------ packet walks */
 /* Propagate to optical depth tau (extinction) or escape, depositing eps*kappa*l per segment
  * into cells holding dust.  Returns 1 on escape, 0 at an interaction point. */
+/* Walk to optical depth tau; *run is the cell of the packet's current run of deposits (-1 at
+ * emission): a deposit in another cell starts a new run, one packet entry of that cell. */
 static int walk_to_tau(const or_model* m, double p[3], const double u[3], int c[3], double tau,
-                       double chi_nu, double dep, double* acc, int64_t* ncross) {
+                       double chi_nu, double dep, double* acc, int64_t* visits, int64_t* run, int64_t* ncross) {
     for (;;) {
         int64_t ci = cell_index(m, c);
         int axis, dir;
@@ -564,10 +568,14 @@ static int walk_to_tau(const or_model* m, double p[3], const double u[3], int c[
         if (tau < dtau) {
             double lp = tau / (rho * chi_nu);
             acc[ci] += dep * lp;
+            if (*run != ci) { visits[ci]++; *run = ci; }
             for (int a = 0; a < 3; ++a) p[a] += lp * u[a];
             return 0;
         }
-        if (rho > 0) acc[ci] += dep * l;
+        if (rho > 0) {
+            acc[ci] += dep * l;
+            if (*run != ci) { visits[ci]++; *run = ci; }
+        }
         tau -= dtau;
         for (int a = 0; a < 3; ++a) p[a] += l * u[a];
         (*ncross)++;
@@ -664,6 +672,7 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
     /* emission (Sect. 2.2, 2.1.1) */
     double p[3], u[3], nu;
     int c[3];
+    int64_t run = -1;      /* cell of the packet's current run of deposits */
     int s = (int)select_cdf(m->nsrc, m->src_cdf, uniform(&rng));
     if (s < m->npoint) {
         p[0] = m->src_pos[3 * s]; p[1] = m->src_pos[3 * s + 1]; p[2] = m->src_pos[3 * s + 2];
@@ -703,7 +712,7 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
     for (;;) {
         double tau = -log(uniform(&rng));
         double dep = eps * (1.0 - alb) * chi;   /* eps * kappa_nu */
-        if (walk_to_tau(m, p, u, c, tau, chi, dep, R->acc, &R->n_crossings)) {
+        if (walk_to_tau(m, p, u, c, tau, chi, dep, R->acc, R->visits, &run, &R->n_crossings)) {
             R->e_escaped += eps;
             int b = sed_bin(m, nu);
             int bm = (int)floor((u[2] + 1.0) * 0.5 * N_ESC_MU);
@@ -778,6 +787,7 @@ int or_run_packets(const or_model* m, const or_params* P, or_result* R) {
         sh[t].R.sed = (double*)calloc((size_t)(sed_len(m) + 1), sizeof(double));
         sh[t].R.img = (double*)calloc((size_t)(img_len(m) + 1), sizeof(double));
         sh[t].R.esc = (double*)calloc((size_t)(esc_len(m) + 1), sizeof(double));
+        sh[t].R.visits = (int64_t*)calloc((size_t)ncells(m), sizeof(int64_t));
         pthread_create(&th[t], NULL, shard_main, &sh[t]);
     }
     for (int t = 0; t < nt; ++t) {
@@ -787,6 +797,7 @@ int or_run_packets(const or_model* m, const or_params* P, or_result* R) {
         for (int64_t i = 0; i < sed_len(m); ++i) R->sed[i] += r->sed[i];
         for (int64_t i = 0; i < img_len(m); ++i) R->img[i] += r->img[i];
         for (int64_t i = 0; i < esc_len(m); ++i) R->esc[i] += r->esc[i];
+        for (int64_t i = 0; i < ncells(m); ++i) R->visits[i] += r->visits[i];
         R->e_escaped += r->e_escaped;
         R->e_killed += r->e_killed;
         R->e_absorbed += r->e_absorbed;
@@ -796,7 +807,7 @@ int or_run_packets(const or_model* m, const or_params* P, or_result* R) {
         R->n_crossings += r->n_crossings;
         R->n_peel_crossings += r->n_peel_crossings;
         R->n_killed += r->n_killed;
-        free(r->acc); free(r->sed); free(r->img); free(r->esc);
+        free(r->acc); free(r->sed); free(r->img); free(r->esc); free(r->visits);
     }
     free(sh);
     free(th);

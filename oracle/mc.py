@@ -85,6 +85,7 @@ class ORResult(C.Structure):
         ("e_escaped", C.c_double), ("e_killed", C.c_double), ("e_absorbed", C.c_double),
         ("n_interactions", C.c_int64), ("n_scatter", C.c_int64), ("n_absorb", C.c_int64),
         ("n_crossings", C.c_int64), ("n_peel_crossings", C.c_int64), ("n_killed", C.c_int64),
+        ("visits", _lp),
     ]
 
 
@@ -271,12 +272,14 @@ class OracleModel:
         sed = np.zeros(max(1, self.nobs * self.wl.nsed))
         img = np.zeros(max(1, self.nobs * self.nimg * self.wl.img_nx * self.wl.img_ny))
         esc = np.zeros(N_ESC_MU * self.wl.nsed)
+        visits = np.zeros(self.nc, np.int64)
         R = ORResult()
         R.acc, R.sed, R.img, R.esc = _ptr(acc), _ptr(sed), _ptr(img), _ptr(esc)
+        R.visits = _ptr(visits, _lp)
         rc = lib().or_run_packets(C.byref(m), C.byref(P), C.byref(R))
         if rc != 0:
             raise RuntimeError("oracle packet loop failed")
-        out = dict(acc=acc, sed=sed[: self.nobs * self.wl.nsed].reshape(self.nobs, self.wl.nsed),
+        out = dict(acc=acc, visits=visits, sed=sed[: self.nobs * self.wl.nsed].reshape(self.nobs, self.wl.nsed),
                    esc=esc.reshape(N_ESC_MU, self.wl.nsed), eps=P.eps,
                    e_escaped=R.e_escaped, e_killed=R.e_killed, e_absorbed=R.e_absorbed,
                    n_interactions=R.n_interactions, n_scatter=R.n_scatter, n_absorb=R.n_absorb,
@@ -285,10 +288,18 @@ class OracleModel:
             out["img"] = img.reshape(self.nobs, self.nimg, self.wl.img_ny, self.wl.img_nx)
         return out
 
+    def chi_rosseland(self):
+        """Rosseland mean extinction on the temperature nodes (App. A)."""
+        if getattr(self, "_chi_r", None) is None:
+            self._chi_r = T.rosseland_mean(self.nu, self.chi, self.T_nodes)
+        return self._chi_r
+
     # ---------------------------------------------------------------- iteration
     def run_iteration(self, n_packets=None, p=0.99, quantity="T", peel=False, update=True,
-                      max_interactions=1_000_000, terminate_on_absorb=False, nthreads=1):
-        """One Lucy iteration (update=True) or one imaging pass (update=False)."""
+                      max_interactions=1_000_000, terminate_on_absorb=False, nthreads=1, pda_min=0):
+        """One Lucy iteration (update=True) or one imaging pass (update=False).  pda_min > 0
+        (spherical grids): cells with dust sampled by fewer than pda_min packet path segments
+        take their temperature from the partial diffusion approximation (App. A)."""
         n = self.wl.n_packets if n_packets is None else int(n_packets)
         key = self.iteration if update else (IMAGING_KEY | self.iteration)
         out = self.run_packets(n, key, peel=peel, max_interactions=max_interactions,
@@ -298,6 +309,14 @@ class OracleModel:
             Tn, _, _ = T.temperature_from_adot(adot, self.T_nodes, self.dust.E)     # Eq. 3
             mask = self.rho > 0
             _, lo, hi = T.temperature_from_adot(adot[mask], self.T_nodes, self.dust.E)
+            n_pda = 0
+            if pda_min > 0 and self.gtype == 1:
+                from . import pda
+                Tn, pmask = pda.solve(self.walls, self.rho, Tn, self.T, out["visits"], pda_min, self.T_nodes,
+                                      self.chi_rosseland())
+                adot = adot.copy()
+                adot[pmask] = T.interp_loglog(Tn[pmask], self.T_nodes, self.dust.E)
+                n_pda = int(pmask.sum())
             prev = self.T if quantity == "T" else self.adot
             cur = Tn if quantity == "T" else adot
             if self.iteration == 0 and quantity != "T":
@@ -308,5 +327,5 @@ class OracleModel:
             self.T = Tn
             self.adot = adot
             self.iteration += 1
-            out.update(adot=adot, T=Tn, Q=Q, Delta=D, clamp_low=lo, clamp_high=hi)
+            out.update(adot=adot, T=Tn, Q=Q, Delta=D, clamp_low=lo, clamp_high=hi, n_pda=n_pda)
         return out

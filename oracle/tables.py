@@ -33,6 +33,32 @@ def planck_bnu(nu, T):
         return 2.0 * H_PLANCK * nu ** 3 / C_LIGHT ** 2 / np.expm1(x)
 
 
+def planck_dbdt(nu, T):
+    """dB_nu/dT = (2 h nu^3 / c^2) (x / T) e^x / (e^x - 1)^2, x = h nu / k T, written with
+    e^x / (e^x - 1)^2 = 1 / (4 sinh^2(x / 2))  [erg/s/cm^2/Hz/sr/K]."""
+    nu = np.asarray(nu, dtype=np.float64)
+    x = H_PLANCK * nu / (K_BOLTZ * T)
+    with np.errstate(over="ignore"):
+        return 2.0 * H_PLANCK * nu ** 3 / C_LIGHT ** 2 * (x / T) / (4.0 * np.sinh(0.5 * x) ** 2)
+
+
+def rosseland_mean(nu, chi, T_nodes):
+    """Rosseland mean extinction chi_R(T) = int dB/dT dnu / int chi_nu^-1 dB/dT dnu (the
+    diffusion coefficient D = 1 / (3 rho chi_R) of App. A), trapezoid rule over the dust nodes."""
+    nu = np.asarray(nu, dtype=np.float64)
+    chi = np.asarray(chi, dtype=np.float64)
+    T_nodes = np.asarray(T_nodes, dtype=np.float64)
+    w = planck_dbdt(nu[None, :], T_nodes[:, None])
+    return trapezoid_pieces(nu, w).sum(axis=-1) / trapezoid_pieces(nu, w / chi[None, :]).sum(axis=-1)
+
+
+def interp_loglog(x, x_nodes, y_nodes):
+    """y(x) linear in log-log between table nodes, clamped to the end values."""
+    lx = np.log(np.asarray(x_nodes, dtype=np.float64))
+    ly = np.log(np.asarray(y_nodes, dtype=np.float64))
+    return np.exp(np.interp(np.log(np.asarray(x, dtype=np.float64)), lx, ly))
+
+
 def kappa_abs(chi, albedo):
     """Mass absorption coefficient kappa_nu = (1 - albedo) chi_nu."""
     return (1.0 - np.asarray(albedo)) * np.asarray(chi)

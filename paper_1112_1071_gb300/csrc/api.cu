@@ -98,6 +98,18 @@ int stage_grid(hrt_ctx* ctx) {
             cph[k] = (float)std::cos(p);
             sph[k] = (float)std::sin(p);
         }
+        // diffusion-approximation geometry (scaled): r centres and widths, radial walls, sin of
+        // the polar centres, polar widths, sin of the polar walls, azimuthal widths
+        std::vector<double> geo;
+        geo.reserve(3 * nr + 3 * nt + np + 2);
+        for (int i = 0; i < nr; ++i) geo.push_back(0.5 * (rwd[i] + rwd[i + 1]));
+        for (int i = 0; i < nr; ++i) geo.push_back(rwd[i + 1] - rwd[i]);
+        for (int i = 0; i <= nr; ++i) geo.push_back(rwd[i]);
+        for (int j = 0; j < nt; ++j) geo.push_back(std::sin(0.5 * (ctx->w[1][j] + ctx->w[1][j + 1])));
+        for (int j = 0; j < nt; ++j) geo.push_back(ctx->w[1][j + 1] - ctx->w[1][j]);
+        for (int j = 0; j <= nt; ++j) geo.push_back(std::sin(ctx->w[1][j]));
+        for (int k = 0; k < np; ++k) geo.push_back(ctx->w[2][k + 1] - ctx->w[2][k]);
+        CK(ctx->d_pgeo.upload(geo.data(), geo.size(), s), "pda geometry");
         CK(ctx->d_rw.upload(rw.data(), rw.size(), s), "walls");
         CK(ctx->d_r2w.upload(r2w.data(), r2w.size(), s), "walls");
         CK(ctx->d_r2wl.upload(r2wl.data(), r2wl.size(), s), "walls");
@@ -162,6 +174,7 @@ int stage_dust(hrt_ctx* ctx) {
     CK(ctx->d_nuf.upload(nuf.data(), nnu, s), "dust");
     CK(ctx->d_nu.upload(ctx->nu.data(), nnu, s), "dust");
     CK(ctx->d_kappa.upload(kappa.data(), nnu, s), "dust");
+    CK(ctx->d_chid.upload(ctx->chi.data(), nnu, s), "dust");
     CK(ctx->d_Tn.upload(ctx->Tn.data(), nT, s), "dust");
     CK(ctx->d_lnT.upload(lnT.data(), nT, s), "dust");
     CK(ctx->d_E.alloc(nT), "tables");
@@ -170,6 +183,10 @@ int stage_dust(hrt_ctx* ctx) {
     CK(launch_emission_tables(nnu, ctx->d_nu.p, ctx->d_kappa.p, nT, ctx->d_Tn.p, ctx->d_E.p, ctx->d_lnE.p,
                               ctx->d_cdf_emit.p, s),
        "emission tables");
+    CK(ctx->d_chiR.alloc(nT), "tables");
+    CK(ctx->d_lnchiR.alloc(nT), "tables");
+    CK(launch_rosseland(nnu, ctx->d_nu.p, ctx->d_chid.p, nT, ctx->d_Tn.p, ctx->d_chiR.p, ctx->d_lnchiR.p, s),
+       "rosseland table");
     DevDust& d = ctx->dust;
     d.nnu = nnu; d.nT = nT;
     d.lnu = ctx->d_lnu.p; d.inv_dlnu = ctx->d_inv_dlnu.p; d.lchi = ctx->d_lchi.p; d.alb = ctx->d_alb.p;
@@ -350,8 +367,11 @@ int hrt_destroy(hrt_ctx* ctx) {
     for (auto* b : {&ctx->d_rwd, &ctx->d_cthd, &ctx->d_sthd, &ctx->d_va, &ctx->d_vb, &ctx->d_vc, &ctx->d_nu,
                     &ctx->d_kappa, &ctx->d_Tn, &ctx->d_lnT, &ctx->d_E, &ctx->d_lnE, &ctx->d_src_cdf, &ctx->d_cell_cdf,
                     &ctx->d_spec_nud, &ctx->d_teff, &ctx->d_unu, &ctx->d_uf, &ctx->d_T, &ctx->d_adot, &ctx->d_acc,
-                    &ctx->d_sed, &ctx->d_img})
+                    &ctx->d_sed, &ctx->d_img, &ctx->d_chid, &ctx->d_chiR, &ctx->d_lnchiR, &ctx->d_pgeo, &ctx->d_pda,
+                    &ctx->d_Tprev, &ctx->d_adotprev, &ctx->d_pda_scal})
         b->release();
+    ctx->d_visits.release(); ctx->d_pda_state.release(); ctx->d_pda_count.release(); ctx->d_pda_flag.release();
+    ctx->d_report.release(); ctx->d_report_count.release();
     ctx->d_uoff.release(); ctx->d_un.release(); ctx->d_img_bin.release(); ctx->d_row.release();
     ctx->d_keys.release(); ctx->d_esc.release(); ctx->d_counters.release(); ctx->d_state.release();
     ctx->d_hist.release(); ctx->d_abort.release(); ctx->d_work.release();
@@ -560,6 +580,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (n_packets < 1 || n_packets > 0xFFFFFFFFll) return ctx->fail(HRT_EINVAL, "n_packets must be in [1, 2^32)");
     if (!(P.p > 0 && P.p <= 1)) return ctx->fail(HRT_EINVAL, "percentile p must be in (0, 1]");
     if (P.max_interactions < 0) return ctx->fail(HRT_EINVAL, "max_interactions < 0");
+    if (P.pda_min_visits < 0 || P.pda_min_visits > 0xFFFFFFFFll)
+        return ctx->fail(HRT_EINVAL, "pda_min_visits must be in [0, 2^32)");
     const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
     if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
         return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");
@@ -599,6 +621,14 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     job.tal.abort_flag = ctx->d_abort.p;
     job.tal.report = ctx->d_report.p;
     job.tal.report_count = ctx->d_report_count.p;
+    // packet entries per cell, for the diffusion approximation of this Lucy iteration
+    const bool pda = P.pda_min_visits > 0 && P.update_temperature && ctx->gtype == GRID_SPHERICAL;
+    job.tal.visits = nullptr;
+    if (pda) {
+        CK(ctx->d_visits.alloc(nc), "alloc visits");
+        CK(cudaMemsetAsync(ctx->d_visits.p, 0, nc * sizeof(uint32_t), s), "zero visits");
+        job.tal.visits = ctx->d_visits.p;
+    }
     RunArgs& A = job.args;
     A = RunArgs{};
     A.n_packets = n_packets;
@@ -642,6 +672,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     CK(e, "propagate");
     CK(cudaEventRecord(ctx->ev[1], s), "event");
     const int64_t k_rank = ctx->n_dust > 0 ? (nc - ctx->n_dust) + (int64_t)std::ceil(P.p * (double)ctx->n_dust) - 1 : 0;
+    PdaStats pda_stats{0, 0, 0.0};
     if (P.update_temperature) {
         TemperatureJob tj;
         tj.gtype = ctx->gtype;
@@ -661,7 +692,57 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         tj.emit_row = ctx->d_row.p;
         tj.keys = ctx->d_keys.p;
         tj.counters = ctx->d_counters.p + N_COUNTERS;
+        if (pda) {
+            CK(ctx->d_Tprev.alloc(nc), "alloc pda");
+            CK(ctx->d_adotprev.alloc(nc), "alloc pda");
+            CK(cudaMemcpyAsync(ctx->d_Tprev.p, ctx->d_T.p, nc * 8, cudaMemcpyDeviceToDevice, s), "pda copy");
+            CK(cudaMemcpyAsync(ctx->d_adotprev.p, ctx->d_adot.p, nc * 8, cudaMemcpyDeviceToDevice, s), "pda copy");
+        }
         CK(launch_temperature(tj, s, &launched), "temperature");
+        if (pda) {
+            CK(ctx->d_pda.alloc((size_t)15 * nc), "alloc pda");
+            CK(ctx->d_pda_state.alloc(nc), "alloc pda");
+            CK(ctx->d_pda_scal.alloc(8), "alloc pda");
+            CK(ctx->d_pda_count.alloc(1), "alloc pda");
+            CK(ctx->d_pda_flag.alloc(1), "alloc pda");
+            PdaJob J;
+            J.n1 = ctx->n[0]; J.n2 = ctx->n[1]; J.n3 = ctx->n[2];
+            J.nc = nc;
+            J.rhoL = ctx->d_rhoL.p;
+            const double* gp = ctx->d_pgeo.p;
+            J.rc = gp; gp += J.n1;
+            J.dr = gp; gp += J.n1;
+            J.rface = gp; gp += J.n1 + 1;
+            J.stc = gp; gp += J.n2;
+            J.dth = gp; gp += J.n2;
+            J.stf = gp; gp += J.n2 + 1;
+            J.dph = gp;
+            J.visits = ctx->d_visits.p;
+            J.n_min = (uint32_t)P.pda_min_visits;
+            J.T_prev = ctx->d_Tprev.p;
+            J.adot_prev = ctx->d_adotprev.p;
+            J.T = ctx->d_T.p; J.adot = ctx->d_adot.p; J.row = ctx->d_row.p; J.keys = ctx->d_keys.p;
+            J.lnT = ctx->d_lnT.p; J.lnE = ctx->d_lnE.p; J.lnchiR = ctx->d_lnchiR.p;
+            J.nT = (int)ctx->Tn.size();
+            J.quantity = P.quantity;
+            J.first = ctx->iteration == 0 ? 1 : 0;
+            J.state = ctx->d_pda_state.p;
+            double* w = ctx->d_pda.p;
+            J.dtau = w; w += 3 * nc;
+            J.W = w; w += 6 * nc;
+            J.x = w; w += nc;
+            J.r = w; w += nc;
+            J.p = w; w += nc;
+            J.q = w; w += nc;
+            J.b = w; w += nc;
+            J.dg = w;
+            J.scal = ctx->d_pda_scal.p;
+            J.count = ctx->d_pda_count.p;
+            J.flag = ctx->d_pda_flag.p;
+            int hflag = 0;
+            double hscal[8];
+            CK(run_pda(J, 1e-12, 100000, &hflag, hscal, &pda_stats, s, &launched), "diffusion approximation");
+        }
         if (ctx->n_dust > 0) {
             int kk = std::max<int64_t>(0, std::min<int64_t>(k_rank, nc - 1));
             CK(launch_select_kth(ctx->d_keys.p, nc, (unsigned long long)kk, ctx->d_hist.p, ctx->d_state.p,
@@ -695,6 +776,10 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
     st.ms_total = ms;
     st.kernel_launches = launched;
+    st.n_pda = pda_stats.n_cells;
+    st.pda_iterations = pda_stats.iterations;
+    st.pda_residual = pda_stats.residual;
+    if (P.update_temperature) ctx->visits_valid = pda;
     const double inf = std::numeric_limits<double>::infinity();
     st.Q = inf;
     st.Delta = inf;
@@ -913,6 +998,26 @@ int hrt_step_temperature(hrt_ctx* ctx, int64_t n, const double* d_adot, double* 
                                  (int)ctx->Tn.size(), ctx->stream),
        "temperature");
     CK(cudaStreamSynchronize(ctx->stream), "temperature");
+    return HRT_OK;
+}
+
+int hrt_get_visits(hrt_ctx* ctx, uint32_t* out, int64_t n) {
+    if (!ctx || !out) return HRT_EINVAL;
+    if (!ctx->visits_valid) return ctx->fail(HRT_ESTATE, "no packet entries counted: run a Lucy iteration with pda_min_visits > 0");
+    if (n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "visits: n must equal the number of cells");
+    DeviceGuard dg(ctx->device);
+    CK(cudaMemcpyAsync(out, ctx->d_visits.p, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream), "visits");
+    CK(cudaStreamSynchronize(ctx->stream), "visits");
+    return HRT_OK;
+}
+
+int hrt_get_rosseland(hrt_ctx* ctx, double* out, int64_t n) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    if (!out || n < (int64_t)ctx->Tn.size()) return ctx->fail(HRT_EINVAL, "rosseland: output too short");
+    DeviceGuard dg(ctx->device);
+    CK(cudaMemcpyAsync(out, ctx->d_chiR.p, ctx->Tn.size() * 8, cudaMemcpyDeviceToHost, ctx->stream), "rosseland");
+    CK(cudaStreamSynchronize(ctx->stream), "rosseland");
     return HRT_OK;
 }
 

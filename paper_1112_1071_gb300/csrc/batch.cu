@@ -121,6 +121,7 @@ int build_batch(hrt_batch* b, const int64_t* n_packets, const hrt_run_params& P)
         M.t.abort_flag = b->d_abort.p;
         M.t.report = b->d_report.p;
         M.t.report_count = b->d_report_count.p;
+        M.t.visits = nullptr;
         RunArgs& A = M.a;
         A.n_packets = n_packets[m];
         A.first_packet = 0;

@@ -105,6 +105,13 @@ struct hrt_ctx {
     DBuf<unsigned long long> d_work;
     DBuf<float> d_report;
     DBuf<unsigned> d_report_count;
+    // ---- partial diffusion approximation (App. A)
+    DBuf<double> d_chid, d_chiR, d_lnchiR, d_pgeo, d_pda, d_Tprev, d_adotprev, d_pda_scal;
+    DBuf<uint32_t> d_visits;
+    DBuf<uint8_t> d_pda_state;
+    DBuf<unsigned long long> d_pda_count;
+    DBuf<int> d_pda_flag;
+    bool visits_valid = false;
     unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // start, after propagation, end, before propagation
     double Q_prev = std::numeric_limits<double>::infinity();

@@ -29,9 +29,10 @@ constexpr float PEEL_TAU_STOP = 40.f;
 
 // Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
 // With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
-// group adds its sum with one FP64 atomic.
+// group adds its sum with one FP64 atomic.  Each flushed run is one packet entry of the cell,
+// counted into `visits` when the diffusion approximation needs it.
 template <bool WAGG>
-__device__ __forceinline__ void flush_deposit(double* acc, bool flushing, int32_t ci, float v) {
+__device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, bool flushing, int32_t ci, float v) {
     if constexpr (WAGG) {
         const unsigned lane = threadIdx.x & 31u;
         const int key = flushing ? ci : -1 - (int)lane;
@@ -39,14 +40,28 @@ __device__ __forceinline__ void flush_deposit(double* acc, bool flushing, int32_
         if (!flushing) return;
         if (__popc(peers) == 1) {
             atomicAdd(acc + ci, widen(v));
+            if (visits) atomicAdd(visits + ci, 1u);
             return;
         }
         float sum = 0.f;
         for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
-        if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(acc + ci, widen(sum));
+        if (lane == (unsigned)(__ffs(peers) - 1)) {
+            atomicAdd(acc + ci, widen(sum));
+            if (visits) atomicAdd(visits + ci, (uint32_t)__popc(peers));
+        }
     } else {
-        if (flushing) atomicAdd(acc + ci, widen(v));
+        if (flushing) {
+            atomicAdd(acc + ci, widen(v));
+            if (visits) atomicAdd(visits + ci, 1u);
+        }
     }
+}
+
+// End of a lane's run outside the walk step (packet end, watchdog, kernel end).
+__device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v) {
+    if (ci < 0) return;
+    if (v != 0.f) atomicAdd(t.acc + ci, widen(v));
+    if (t.visits) atomicAdd(t.visits + ci, 1u);
 }
 
 // The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
@@ -126,12 +141,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
             r[13] = pk.nu; r[14] = (float)pobs; r[15] = (float)where;
         }
-        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
+        flush_run(t, dep_ci, dep_val);
         dep_ci = -1;
         mode = M_DONE;
     };
     auto end_packet = [&]() {
-        if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
+        flush_run(t, dep_ci, dep_val);
         dep_ci = -1;
         dep_val = 0.f;
         lc.v[C_PACKETS_DONE]++;
@@ -291,12 +306,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     ray_steps = 0;
                 }
             }
-            flush_deposit<WAGG>(t.acc, flushing, fci, fval);
+            flush_deposit<WAGG>(t.acc, t.visits, flushing, fci, fval);
             if (((++steps) & 4095u) == 0) watchdog(steps);
         }
         if (((++rounds) & 255u) == 0) watchdog(rounds);
     }
-    if (dep_ci >= 0 && dep_val != 0.f) atomicAdd(t.acc + dep_ci, widen(dep_val));
+    flush_run(t, dep_ci, dep_val);
 }
 
 // ---------------------------------------------------------------- one model

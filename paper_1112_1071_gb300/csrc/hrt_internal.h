@@ -82,6 +82,41 @@ cudaError_t launch_invert_temperature(const double* adot, double* T, int64_t n, 
                                       const double* lnT, const double* Tn, int nT, cudaStream_t s);
 cudaError_t launch_emit_rows(const double* T, int32_t* rows, int64_t n, const double* lnT, int nT, cudaStream_t s);
 
+// pda.cu: partial diffusion approximation (App. A), spherical-polar grids
+struct PdaJob {
+    int32_t n1, n2, n3;
+    int64_t nc;
+    const float* rhoL;                       // rho L0
+    const double *rc, *dr, *rface;           // [n1] centre, width; [n1+1] walls (scaled)
+    const double *stc, *dth, *stf;           // [n2] sin(theta centre), dtheta; [n2+1] sin(theta walls)
+    const double* dph;                       // [n3]
+    const uint32_t* visits;                  // packet entries per cell in this iteration
+    uint32_t n_min;                          // cells with dust and fewer entries are solved
+    const double* T_prev;                    // temperatures the iteration started from (chi_R, keys)
+    const double* adot_prev;
+    double* T;                               // in: Monte-Carlo T of this iteration, out: after the PDA
+    double* adot;
+    int32_t* row;
+    unsigned long long* keys;
+    const double *lnT, *lnE, *lnchiR;        // [nT] tables
+    int32_t nT;
+    int32_t quantity, first;
+    uint8_t* state;                          // 0 Monte-Carlo, 1 candidate, 2 solved
+    double *dtau, *W, *x, *r, *p, *q, *b, *dg;   // [3][nc], [6][nc], [nc] x 6
+    double* scal;                            // [8] CG scalars
+    unsigned long long* count;
+    int* flag;
+};
+struct PdaStats {
+    int64_t n_cells;
+    int64_t iterations;
+    double residual;                         // |b - A x| / |b| at exit
+};
+cudaError_t launch_rosseland(int nnu, const double* nu, const double* chi, int nT, const double* T, double* chiR,
+                             double* lnchiR, cudaStream_t s);
+cudaError_t run_pda(const PdaJob& J, double tol, int max_iter, int* host_flag, double* host_scal, PdaStats* st,
+                    cudaStream_t s, int* launched);
+
 // tables.cu (FP64 table construction on the device)
 cudaError_t launch_emission_tables(int nnu, const double* nu, const double* kappa, int nT, const double* T,
                                    double* E, double* lnE, float* cdf, cudaStream_t s);

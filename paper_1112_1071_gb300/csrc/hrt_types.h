@@ -88,6 +88,8 @@ struct Tallies {
     int32_t* abort_flag;           // set by the watchdog
     float* report;                 // [WD_REPORTS][WD_FIELDS] state of lanes stopped by the watchdog
     unsigned* report_count;
+    uint32_t* visits;              // [ncells] packet entries (runs of one packet's segments in the
+                                   // cell), counted for the diffusion approximation; null = off
 };
 
 constexpr int WD_REPORTS = 32;

@@ -57,6 +57,7 @@ struct Packet {
     float3 last_origin;      // emission position (before any hole crossing)
     int32_t emit_relocate;   // 1: emission peel rays must locate their cell along the observer
     int32_t src;             // emitting source
+    int32_t run_ci;          // cell of the current run of deposits (plain kernel's entry count)
 };
 
 __device__ __forceinline__ void set_frequency(Packet& pk, const DevDust& d, const DevObs& o, float nu) {
@@ -117,6 +118,7 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
     pk.nint = 0;
     const int src = (int)select_cdf<double>(s.cdf, s.nsrc, (double)pk.rng.next());
     pk.src = src;
+    pk.run_ci = -1;
     if (src < s.npoint) {
         pk.r.p = make_float3(__ldg(s.pos + 3 * src), __ldg(s.pos + 3 * src + 1), __ldg(s.pos + 3 * src + 2));
         const float u1 = pk.rng.next(), u2 = pk.rng.next();

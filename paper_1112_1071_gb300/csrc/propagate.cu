@@ -36,6 +36,10 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
         const float rho = __ldg(g.rhoL + pk.r.ci);
         const float k = rho * chi;
         const float dtau = k * l;
+        if (rho > 0.f && t.visits && pk.r.ci != pk.run_ci) {    // a new run: one packet entry
+            atomicAdd(t.visits + pk.r.ci, 1u);
+            pk.run_ci = pk.r.ci;
+        }
         if (tau < dtau) {
             const float lp = tau / k;
             atomicAdd(t.acc + pk.r.ci, (double)(kap * lp));

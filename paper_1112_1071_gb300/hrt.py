@@ -38,6 +38,7 @@ class hrt_run_params(C.Structure):
         ("q_thres", C.c_double), ("delta_thres", C.c_double), ("kernel", C.c_int32),
         ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("regroup_threshold", C.c_int32),
         ("watchdog_ms", C.c_double), ("first_packet", C.c_int64), ("n_total", C.c_int64),
+        ("pda_min_visits", C.c_int64),
     ]
 
 
@@ -49,7 +50,8 @@ class hrt_iter_stats(C.Structure):
         ("n_scatter", C.c_int64), ("n_absorb", C.c_int64), ("n_crossings", C.c_int64),
         ("n_peel_crossings", C.c_int64), ("n_killed", C.c_int64), ("clamp_low", C.c_int64),
         ("clamp_high", C.c_int64), ("ms_propagate", C.c_double), ("ms_total", C.c_double),
-        ("kernel_launches", C.c_int64),
+        ("kernel_launches", C.c_int64), ("n_pda", C.c_int64), ("pda_iterations", C.c_int64),
+        ("pda_residual", C.c_double),
     ]
 
     def as_dict(self):
@@ -102,6 +104,8 @@ _SIGS = {
     "hrt_step_sample_source": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
     "hrt_step_temperature": (C.c_int, [_vp, _i64, _vp, _vp]),
     "hrt_get_tables": (C.c_int, [_vp, _vp, _i64, _vp, _i64]),
+    "hrt_get_rosseland": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_get_visits": (C.c_int, [_vp, _vp, _i64]),
     "hrt_quantile_ratio_noalloc": (C.c_int, [_i64, _vp, _vp, _vp, C.c_double, _vp, _vp]),
     "hrt_net_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_uint64, _vp]),
     "hrt_net_destroy": (C.c_int, [_vp]),
@@ -283,6 +287,14 @@ class Model:
         cdf = np.empty(nT * nnu, dtype=np.float32)
         check(self.ctx, load().hrt_get_tables(self.ctx, _ptr(E), nT, _ptr(cdf), cdf.size))
         return E, cdf.reshape(nT, nnu)
+
+    def rosseland(self):
+        out = np.empty(len(self.wl.T_nodes))
+        check(self.ctx, load().hrt_get_rosseland(self.ctx, _ptr(out), out.size))
+        return out
+
+    def visits(self):
+        return self._get("hrt_get_visits", self.ncells, np.uint32)
 
     # ---- single steps on torch CUDA tensors
     def step(self, name, *args):
