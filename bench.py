@@ -16,6 +16,11 @@ e2e       the same step through the C ABI with host buffers: density and startin
 roofline  the propagation kernel: algorithmic bytes per launch (20 B per packet cell crossing:
           FP32 density + FP64 accumulator read-modify-write; 4 B per peel-off crossing; 400 B per
           re-emission row) over its measured duration, against the measured HBM copy bandwidth.
+time_to_converged_ms      device time of the Lucy iterations until the 99th percentile of the
+          iteration change in T is below 2 % (null when the 10 iterations never get there: the
+          Monte-Carlo noise of the disk's optically thick midplane is then the floor).
+time_to_converged_pda_ms  the same from a separate solve (not in `value`) in which cells entered
+          by fewer than --pda-min packets take the partial diffusion approximation (App. A).
 
 ``--impl reference`` times the FP64 CPU oracle (the reference implementation of this build) on
 the host cores on a bounded sample of the same workload.  N > 1 GPUs (torchrun) run independent
@@ -54,6 +59,9 @@ def parse():
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pda-min", type=int, default=6000,
+                    help="packet entries below which a cell takes the diffusion approximation in the "
+                         "time-to-converged solve with PDA (App. A); 0 skips that solve")
     return ap.parse_args()
 
 
@@ -245,6 +253,24 @@ def main():
                 it_conv = i + 1
                 break
         conv.append((it_conv, t if it_conv else None))
+    # time to the 2% criterion with the partial diffusion approximation (App. A) for the cells
+    # entered by fewer than --pda-min packets (not part of the timed throughput steps)
+    conv_pda, pda_q, pda_cells = [], [], 0
+    if args.pda_min > 0:
+        for _ in range(args.steps):
+            hrt.check(m.ctx, L.hrt_set_temperature_device(m.ctx, T0.data_ptr(), nc))
+            hrt.check(m.ctx, L.hrt_set_iteration(m.ctx, 0))
+            t, it_conv, qh = 0.0, None, []
+            for i in range(args.iters):
+                s = m.run_iteration(n_packets=args.packets, kernel=kern, pda_min_visits=args.pda_min)
+                t += s["ms_total"]
+                qh.append(round(s["Q"], 5))
+                pda_cells = s["n_pda"]
+                if s["converged"] and i > 0:
+                    it_conv = i + 1
+                    break
+            conv_pda.append((it_conv, t if it_conv else None))
+            pda_q = qh
     barrier()
     clk = clocks.stop()
 
@@ -297,6 +323,11 @@ def main():
             "time_to_converged_ms": statistics.median(done) if done else None,
             "q99_history": [round(s["Q"], 5) for s in last[:-1]],
             "iterations_to_converged": statistics.median([i for i in its if i]) if any(its) else None,
+            "time_to_converged_pda_ms": statistics.median([t for _, t in conv_pda if t is not None])
+            if any(t is not None for _, t in conv_pda) else None,
+            "pda": {"min_visits": args.pda_min, "cells": pda_cells, "q99_history": pda_q,
+                    "iterations_to_converged": statistics.median([i for i, _ in conv_pda if i])
+                    if any(i for i, _ in conv_pda) else None} if args.pda_min > 0 else None,
             "crossings_per_step": sum(s["n_crossings"] for s in last),
             "peel_crossings_per_step": sum(s["n_peel_crossings"] for s in last),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -66,7 +66,7 @@ __device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v)
 
 // The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
 // `need` (ballot) lanes want a packet and returns this lane's packet id, or -1 when none is left.
-template <int G, bool WAGG, class Fetch>
+template <int G, bool WAGG, bool PEEL, class Fetch>
 __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, const DevSources& s, const DevObs& o,
                                            const RunArgs& a, const Tallies& t, const SharedTallies& st,
                                            LocalCounters& lc, Fetch&& fetch) {
@@ -112,15 +112,17 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     };
     // after an emission or interaction: peel (if wanted) then draw a new optical depth
     auto after_event = [&](int kind, int relocate) {
-        if (a.peel && pk.sbin >= 0 && o.nobs > 0) {
-            saved = pk.r;
-            pkind = kind;
-            prelocate = relocate;
-            pobs = 0;
-            start_peel(0);
-        } else {
-            start_walk();
+        if constexpr (PEEL) {
+            if (a.peel && pk.sbin >= 0 && o.nobs > 0) {
+                saved = pk.r;
+                pkind = kind;
+                prelocate = relocate;
+                pobs = 0;
+                start_peel(0);
+                return;
+            }
         }
+        start_walk();
     };
     // Watchdog (warp-uniform call): past the time budget, every live lane stops, records its
     // state in the report buffer (first WD_REPORTS lanes) and is counted; nothing traps.
@@ -151,6 +153,36 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         dep_val = 0.f;
         lc.v[C_PACKETS_DONE]++;
         mode = M_NEED;
+    };
+
+    // A peel ray has ended (edge, tau stop, precomputed column or start outside): tally its weight
+    // eps p exp(-tau) into the SED (and image) bins and start the next observer's ray, or give the
+    // lane back to its packet.  Called from the event phase and, so that a lane walking its peel
+    // rays never waits for the warp's next event phase, from the walk step itself.
+    auto finish_peels = [&]() {
+        do {
+            const float3 n = make_float3(__ldg(o.n + 3 * pobs), __ldg(o.n + 3 * pobs + 1), __ldg(o.n + 3 * pobs + 2));
+            const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
+            const double w = a.eps * (double)(prob * expf(-tau));
+            if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
+            else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
+            if (o.nimg > 0) {
+                const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
+                const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
+                const int ix = (int)floorf((px + o.img_half) * o.img_scale);
+                const int iy = (int)floorf((py + o.img_half) * o.img_scale);
+                if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
+                    for (int l = 0; l < o.nimg; ++l)
+                        if (__ldg(o.img_bin + l) == pk.sbin)
+                            atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
+            }
+            if (++pobs < o.nobs) {
+                start_peel(pobs);
+            } else {
+                pk.r = saved;
+                start_walk();
+            }
+        } while (mode == M_PEEL_DONE);
     };
 
     for (;;) {
@@ -191,30 +223,8 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     after_event(PEEL_HG, 0);
                 }
             }
-        } else if (mode == M_PEEL_DONE) {
-            do {   // peel rays that need no walk (precomputed columns, start outside) end here
-                const float3 n = make_float3(__ldg(o.n + 3 * pobs), __ldg(o.n + 3 * pobs + 1), __ldg(o.n + 3 * pobs + 2));
-                const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
-                const double w = a.eps * (double)(prob * expf(-tau));
-                if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
-                else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
-                if (o.nimg > 0) {
-                    const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
-                    const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
-                    const int ix = (int)floorf((px + o.img_half) * o.img_scale);
-                    const int iy = (int)floorf((py + o.img_half) * o.img_scale);
-                    if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
-                        for (int l = 0; l < o.nimg; ++l)
-                            if (__ldg(o.img_bin + l) == pk.sbin)
-                                atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
-                }
-                if (++pobs < o.nobs) {
-                    start_peel(pobs);
-                } else {
-                    pk.r = saved;
-                    start_walk();
-                }
-            } while (mode == M_PEEL_DONE);
+        } else if (PEEL && mode == M_PEEL_DONE) {
+            finish_peels();
         }
         // refill: lanes without a packet take the next ids
         const unsigned need = __ballot_sync(FULL, mode == M_NEED);
@@ -251,7 +261,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 const float rho = __ldg(g.rhoL + pk.r.ci);
                 const float k = rho * pk.dust.chi;
                 bool stop = false;
-                if (mode == M_WALK) {
+                if (!PEEL || mode == M_WALK) {
                     const float dtau = k * l;
                     float seg = l;
                     if (tau < dtau) {
@@ -306,6 +316,9 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     ray_steps = 0;
                 }
             }
+            if constexpr (PEEL) {
+                if (mode == M_PEEL_DONE) finish_peels();
+            }
             flush_deposit<WAGG>(t.acc, t.visits, flushing, fci, fval);
             if (((++steps) & 4095u) == 0) watchdog(steps);
         }
@@ -315,8 +328,9 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
 }
 
 // ---------------------------------------------------------------- one model
-// MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80)
-template <int G, bool WAGG, int MINB>
+// MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80);
+// PEEL = imaging pass (peel-off rays walked), compiled out of the Lucy iterations' kernel.
+template <int G, bool WAGG, int MINB, bool PEEL>
 __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
     const SharedTallies st = shared_tallies(o, a);
     LocalCounters lc;
@@ -330,9 +344,15 @@ __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSo
         const unsigned long long q = base + __popc(need & lt_mask);
         return q < (unsigned long long)a.n_packets ? (long long)(a.first_packet + (int64_t)q) : -1ll;
     };
-    event_loop<G, WAGG>(g, d, s, o, a, t, st, lc, fetch);
+    event_loop<G, WAGG, PEEL>(g, d, s, o, a, t, st, lc, fetch);
     flush_counters(lc, t.counters);
     flush_shared(o, a, t, st);
+}
+
+template <int G, bool PEEL>
+static cudaError_t launch_event_shape(const PropagateJob& j, const Launch& l, int bps, cudaStream_t s) {
+    if (bps >= 3) return launch_persistent(k_event<G, true, 3, PEEL>, j, l, s);
+    return launch_persistent(k_event<G, true, 2, PEEL>, j, l, s);
 }
 
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched) {
@@ -340,17 +360,21 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     Launch ll = l;
     ll.block = 256;
     PropagateJob j = job;
-    j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : DEFAULT_REGROUP;
+    const bool peel = job.args.peel != 0;
+    // default shapes (measured on GB300): 3 blocks of 256 per SM (80 registers); warps stay in
+    // the walk phase while at least 20 (spherical Lucy iteration) or 24 (imaging pass; Cartesian
+    // runs of >= 4M packets) lanes walk, 12 for small Cartesian runs whose tail dominates
+    int rg_default = DEFAULT_REGROUP;
+    if (job.grid.type == GRID_SPHERICAL) rg_default = peel ? 24 : 20;
+    else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 24;
+    j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
-    // default shape (measured on GB300): the Cartesian walk gains from 3 blocks/SM at 80
-    // registers, the spherical walk needs the 128-register budget of 2 blocks/SM
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (job.grid.type == GRID_CARTESIAN ? 3 : 2);
-    if (bps >= 3) {
-        if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true, 3>, j, ll, s);
-        return launch_persistent(k_event<GRID_SPHERICAL, true, 3>, j, ll, s);
-    }
-    if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_event<GRID_CARTESIAN, true, 2>, j, ll, s);
-    return launch_persistent(k_event<GRID_SPHERICAL, true, 2>, j, ll, s);
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
+    if (job.grid.type == GRID_CARTESIAN)
+        return peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
+                    : launch_event_shape<GRID_CARTESIAN, false>(j, ll, bps, s);
+    return peel ? launch_event_shape<GRID_SPHERICAL, true>(j, ll, bps, s)
+                : launch_event_shape<GRID_SPHERICAL, false>(j, ll, bps, s);
 }
 
 // ---------------------------------------------------------------- many models, one launch
@@ -381,7 +405,7 @@ __global__ void __launch_bounds__(256, 2) k_event_batch(const BatchModel* __rest
         };
         LocalCounters lc;
         lc.zero();
-        event_loop<G, WAGG>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
+        event_loop<G, WAGG, false>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
         flush_counters(lc, M.t.counters);
     }
 }
