@@ -327,10 +327,16 @@ int hrt_batch_tune(hrt_batch* b, const int64_t* n_packets) {
             return HRT_OK;
         }
     }
-    int rc = build_batch(b, n_packets, P);
+    // trial launches on at most ~2^24 packets in all (each model's budget scaled alike)
+    int64_t total = 0;
+    for (size_t m = 0; m < b->models.size(); ++m) total += n_packets[m];
+    const double scale = total > ((int64_t)1 << 24) ? (double)((int64_t)1 << 24) / (double)total : 1.0;
+    std::vector<int64_t> trial(b->models.size());
+    for (size_t m = 0; m < trial.size(); ++m) trial[m] = std::max<int64_t>(1, (int64_t)(n_packets[m] * scale));
+    int rc = build_batch(b, trial.data(), P);
     if (rc != HRT_OK) return rc;
-    const int regroups[] = {8, 12, 16, 24};
-    const int per_sm[] = {1, 2};
+    const int regroups[] = {12, 16, 20, 24};
+    const int per_sm[] = {2, 3};
     float best = 1e30f;
     Launch best_l = b->launch;
     for (int bp : per_sm) {

@@ -378,8 +378,8 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
 }
 
 // ---------------------------------------------------------------- many models, one launch
-template <int G, bool WAGG>
-__global__ void __launch_bounds__(256, 2) k_event_batch(const BatchModel* __restrict__ models,
+template <int G, bool WAGG, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_event_batch(const BatchModel* __restrict__ models,
                                                         const BatchChunk* __restrict__ chunks, int nchunks,
                                                         unsigned* chunk_counter, const BatchState* __restrict__ state,
                                                         int regroup) {
@@ -410,22 +410,30 @@ __global__ void __launch_bounds__(256, 2) k_event_batch(const BatchModel* __rest
     }
 }
 
+template <int G, int MINB>
+static void launch_batch_shape(const BatchModel* models, const BatchChunk* chunks, int nchunks, unsigned* chunk_counter,
+                               const BatchState* state, int want_per_sm, int regroup, int sms, cudaStream_t s) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<G, true, MINB>, 256, 0);
+    if (want_per_sm > 0 && want_per_sm < per_sm) per_sm = want_per_sm;
+    k_event_batch<G, true, MINB><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks, chunk_counter,
+                                                                                state, regroup);
+}
+
+// Default shape as for one model: 3 blocks of 256 per SM, regroup 20; the autotuner times others.
 cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const BatchChunk* chunks, int nchunks,
                                    unsigned* chunk_counter, const BatchState* state, const Launch& l, cudaStream_t s) {
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : DEFAULT_REGROUP;
+    const int regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : 20;
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
     if (gtype == GRID_CARTESIAN) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<GRID_CARTESIAN, true>, 256, 0);
-        if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
-        k_event_batch<GRID_CARTESIAN, true><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks,
-                                                                                            chunk_counter, state, regroup);
+        if (bps >= 3) launch_batch_shape<GRID_CARTESIAN, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        else launch_batch_shape<GRID_CARTESIAN, 2>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<GRID_SPHERICAL, true>, 256, 0);
-        if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
-        k_event_batch<GRID_SPHERICAL, true><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks,
-                                                                                            chunk_counter, state, regroup);
+        if (bps >= 3) launch_batch_shape<GRID_SPHERICAL, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        else launch_batch_shape<GRID_SPHERICAL, 2>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
     }
     return cudaGetLastError();
 }
