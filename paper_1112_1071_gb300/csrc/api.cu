@@ -126,10 +126,12 @@ int stage_grid(hrt_ctx* ctx) {
         g.thw = ctx->d_thw.p; g.cth = ctx->d_cth.p; g.sth = ctx->d_sth.p; g.cthd = ctx->d_cthd.p; g.sthd = ctx->d_sthd.p;
         g.phw = ctx->d_phw.p; g.cph = ctx->d_cph.p; g.sph = ctx->d_sph.p;
         g.r0 = rw[0];
-        // FP64 sphere coefficients for the shells within 25% of the inner radius (or of the
-        // first wall without a hole), FP64 cone coefficients within sin(theta) < 0.1 of the axis
-        g.r_fp64 = (float)(1.25 * (rwd[0] > 0 ? rwd[0] : rwd[1]));
-        g.sin_fp64 = 0.1f;
+        // FP64 sphere coefficients in the innermost shell (next to the hole, or around the
+        // origin without one) and FP64 cone coefficients for walls within sin(theta) < 0.02 of the
+        // axis.  Measured on the flared disk: the same in all shells within 1.25 r_in and for
+        // sin(theta) < 0.1 cost 1.3x in walk time, with no change in the parity tests.
+        g.r_fp64 = (float)(rwd[1] * (1.0 + 1e-6));
+        g.sin_fp64 = 0.02f;
         for (int i = 0; i < nr; ++i) va[i] = (std::pow(ctx->w[0][i + 1], 3) - std::pow(ctx->w[0][i], 3)) / 3.0;
         for (int j = 0; j < nt; ++j) vb[j] = std::cos(ctx->w[1][j]) - std::cos(ctx->w[1][j + 1]);
         for (int k = 0; k < np; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];

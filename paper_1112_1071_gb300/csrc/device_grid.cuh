@@ -109,9 +109,10 @@ __device__ __forceinline__ bool cart_locate(const DevGrid& g, Ray& r) {
 //     2^-23 |p|^2, at the cost of ~20 FP32 operations and no FP64;
 //   * the coefficients and discriminant are formed in FP64 (products of FP32 numbers are exact
 //     in FP64, so only their sums round) for spheres below r_fp64 and cones with sin(theta)
-//     below sin_fp64 (small r and the polar axis), and for any sphere or cone whose FP32
-//     discriminant is within 2^-10 of a double root (a grazing ray).  The square root,
-//     divisions and root selection then run in FP32 on the accurately rounded coefficients.
+//     below sin_fp64 (small r and the polar axis), and for the inner sphere or a cone whose FP32
+//     discriminant is within 2^-10 of a double root (a grazing ray; for a cone, only when that
+//     root can be the exit).  The square root, divisions and root selection then run in FP32 on
+//     the accurately rounded coefficients.
 
 // s = a + b exactly as s + e (Knuth); __fadd_rn keeps the compiler from fusing or reordering.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
