@@ -134,6 +134,8 @@ typedef struct {
     int32_t peel;
     int32_t terminate_on_absorb;
     int32_t nthreads;
+    int32_t raytrace;         /* 1: point-source emission and dust re-emission reach the SEDs and
+                                 images by raytracing (Sect. 2.6.3), so they are not peeled off */
 } or_params;
 
 typedef struct {
@@ -658,6 +660,51 @@ static void peel(const or_model* m, const double p[3], const int c[3], const dou
     }
 }
 
+/* ------------------------------------------------------------------ raytracing (Sect. 2.6.3) */
+/* Dust-emission rays: ray k draws from its own Philox stream (key, counter (draw/4, k, iter_key,
+ * model)): u0 picks the cell from the cumulative emitted luminosity cdf_L (smallest index with
+ * cdf >= u0), u1..u3 place it uniformly in the cell's volume (as a cell source).  For every
+ * observer the column sum rho l from that point to the grid edge is returned (chi = 1). */
+int or_raytrace_rays(const or_model* m, const or_params* P, int64_t n_rays, const double* cdf_L,
+                     int64_t* cells, double* pos, double* col) {
+    for (int64_t k = 0; k < n_rays; ++k) {
+        rng_t rng;
+        memset(&rng, 0, sizeof(rng));
+        rng.key[0] = P->key[0];
+        rng.key[1] = P->key[1];
+        rng.pkt = (uint32_t)k;
+        rng.iter = P->iter_key;
+        rng.model = P->model_key;
+        int64_t ci = select_cdf(ncells(m), cdf_L, uniform(&rng));
+        int c[3];
+        c[0] = (int)(ci % m->n[0]);
+        c[1] = (int)((ci / m->n[0]) % m->n[1]);
+        c[2] = (int)(ci / ((int64_t)m->n[0] * m->n[1]));
+        double f0 = uniform(&rng), f1 = uniform(&rng), f2 = uniform(&rng);
+        double p[3];
+        if (m->gtype == 0) {
+            double f[3] = {f0, f1, f2};
+            for (int a = 0; a < 3; ++a) p[a] = m->w[a][c[a]] + f[a] * (m->w[a][c[a] + 1] - m->w[a][c[a]]);
+        } else {
+            double r0 = m->w[0][c[0]], r1 = m->w[0][c[0] + 1];
+            double r = cbrt(r0 * r0 * r0 + f0 * (r1 * r1 * r1 - r0 * r0 * r0));
+            double ct0 = cos(m->w[1][c[1]]), ct1 = cos(m->w[1][c[1] + 1]);
+            double ct = ct0 + f1 * (ct1 - ct0);
+            double ph = m->w[2][c[2]] + f2 * (m->w[2][c[2] + 1] - m->w[2][c[2]]);
+            double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            p[0] = r * st * cos(ph); p[1] = r * st * sin(ph); p[2] = r * ct;
+        }
+        cells[k] = ci;
+        for (int a = 0; a < 3; ++a) pos[3 * k + a] = p[a];
+        for (int o = 0; o < m->nobs; ++o) {
+            int64_t nc = 0;
+            int cc[3] = {c[0], c[1], c[2]};
+            col[k * m->nobs + o] = tau_to_edge(m, p, m->obs_n + 3 * o, cc, 1.0, &nc);
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ one packet history */
 static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_result* R) {
     rng_t rng;
@@ -681,7 +728,7 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
         nu = or_sample_table(m->nspec, m->spec_nu, m->spec_cdf + (int64_t)s * m->nspec, uniform(&rng));
         double p0[3] = {p[0], p[1], p[2]};
         if (grid_locate(m, p, u, c) < 0) { R->e_escaped += eps; return; }
-        if (P->peel) peel(m, p0, c, u, nu, eps, PEEL_EMIT, R);
+        if (P->peel && !P->raytrace) peel(m, p0, c, u, nu, eps, PEEL_EMIT, R);
     } else {
         int64_t ci = select_cdf(ncells(m), m->cell_cdf, uniform(&rng));
         c[0] = (int)(ci % m->n[0]);
@@ -734,7 +781,7 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
             int row = m->emit_row[cell_index(m, c)];
             nu = or_sample_table(m->nnu, m->nu, m->cdf_emit + (int64_t)row * m->nnu, uniform(&rng));
             dust_at(m, nu, &chi, &alb);
-            if (P->peel) peel(m, p, c, u, nu, eps, PEEL_REEMIT, R);
+            if (P->peel && !P->raytrace) peel(m, p, c, u, nu, eps, PEEL_REEMIT, R);
         } else {
             R->n_scatter++;
             double mu = or_hg_mu(m->g, uniform(&rng));

@@ -75,7 +75,7 @@ class ORParams(C.Structure):
         ("n_packets", C.c_int64), ("first_packet", C.c_int64), ("key", C.c_uint32 * 2),
         ("iter_key", C.c_uint32), ("model_key", C.c_uint32), ("eps", C.c_double),
         ("max_interactions", C.c_int64), ("peel", C.c_int32), ("terminate_on_absorb", C.c_int32),
-        ("nthreads", C.c_int32),
+        ("nthreads", C.c_int32), ("raytrace", C.c_int32),
     ]
 
 
@@ -110,6 +110,8 @@ def _declare(L):
     L.or_locate.restype = C.c_int
     L.or_trace.argtypes = [C.POINTER(ORModel), _dp, _dp, C.c_int64, _lp, _dp]
     L.or_trace.restype = C.c_int64
+    L.or_raytrace_rays.argtypes = [C.POINTER(ORModel), C.POINTER(ORParams), C.c_int64, _dp, _lp, _dp, _dp]
+    L.or_raytrace_rays.restype = C.c_int
     L.or_tau_to_edge.argtypes = [C.POINTER(ORModel), _dp, _dp, C.c_double]
     L.or_tau_to_edge.restype = C.c_double
     L.or_sed_bin.argtypes = [C.POINTER(ORModel), C.c_double]
@@ -251,9 +253,10 @@ class OracleModel:
 
     # ---------------------------------------------------------------- packets
     def run_packets(self, n_packets, iter_key, peel=False, max_interactions=1_000_000,
-                    terminate_on_absorb=False, nthreads=1, first_packet=0, n_total=None):
+                    terminate_on_absorb=False, nthreads=1, first_packet=0, n_total=None, raytrace=False):
         """Propagate packets first_packet .. first_packet+n_packets-1 with the temperatures held
-        now; eps = L_tot / n_total (dt = 1 s)."""
+        now; eps = L_tot / n_total (dt = 1 s).  With raytrace, point-source emission and dust
+        re-emission are not peeled off (they reach the SEDs by raytracing, Sect. 2.6.3)."""
         n_total = n_packets if n_total is None else n_total
         emit_row = T.emission_row(self.T, self.T_nodes)
         m = self.struct(emit_row)
@@ -268,6 +271,7 @@ class OracleModel:
         P.peel = int(bool(peel))
         P.terminate_on_absorb = int(bool(terminate_on_absorb))
         P.nthreads = int(nthreads)
+        P.raytrace = int(bool(raytrace))
         acc = np.zeros(self.nc)
         sed = np.zeros(max(1, self.nobs * self.wl.nsed))
         img = np.zeros(max(1, self.nobs * self.nimg * self.wl.img_nx * self.wl.img_ny))
