@@ -145,6 +145,13 @@ typedef struct {
                                     (a packet's consecutive path segments in a cell count once) take T
                                     from the discrete diffusion equation of App. A, with well-sampled
                                     neighbours as boundary values; 0 (default) = off; < 2^32 */
+    int64_t raytrace_rays;       /* imaging passes (update_temperature 0, peel 1): > 0 raytraces the
+                                    point-source and dust emission into the SED and image bins
+                                    (Sect. 2.6.3) instead of peeling it off: each source along its one
+                                    ray, the dust by this many rays that start at points drawn in
+                                    proportion to the cells' emission m E(T), each carrying
+                                    L_dust / raytrace_rays over all bins at once; scattered light is
+                                    still peeled off.  0 (default) = off; < 2^32 */
 } hrt_run_params;
 
 typedef struct {

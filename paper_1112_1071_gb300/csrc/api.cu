@@ -54,6 +54,7 @@ int stage_grid(hrt_ctx* ctx) {
     std::vector<float> rhoL(nc);
     for (int64_t c = 0; c < nc; ++c) rhoL[c] = (float)((double)ctx->rho[c] * ctx->L0);
     CK(ctx->d_rhoL.upload(rhoL.data(), nc, s), "upload density");
+    CK(ctx->d_rho.upload(ctx->rho.data(), nc, s), "upload density");
     DevGrid& g = ctx->grid;
     g = DevGrid{};
     g.type = ctx->gtype;
@@ -373,6 +374,13 @@ int hrt_destroy(hrt_ctx* ctx) {
                     &ctx->d_Tprev, &ctx->d_adotprev, &ctx->d_pda_scal})
         b->release();
     ctx->d_visits.release(); ctx->d_pda_state.release(); ctx->d_pda_count.release(); ctx->d_pda_flag.release();
+    for (auto* b : {&ctx->d_rho, &ctx->d_rt_qd_w, &ctx->d_rt_qd_chi, &ctx->d_rt_qs_w, &ctx->d_rt_qs_chi,
+                    &ctx->d_rt_inv_dnu, &ctx->d_rt_col})
+        b->release();
+    for (auto* b : {&ctx->d_rt_qd_off, &ctx->d_rt_qd_j, &ctx->d_rt_qd_bin, &ctx->d_rt_qs_off, &ctx->d_rt_qs_j,
+                    &ctx->d_rt_qs_bin, &ctx->d_rt_row})
+        b->release();
+    for (auto* b : {&ctx->d_rt_cdf, &ctx->d_rt_sums, &ctx->d_rt_total, &ctx->d_src_L}) b->release();
     ctx->d_report.release(); ctx->d_report_count.release();
     ctx->d_uoff.release(); ctx->d_un.release(); ctx->d_img_bin.release(); ctx->d_row.release();
     ctx->d_keys.release(); ctx->d_esc.release(); ctx->d_counters.release(); ctx->d_state.release();
@@ -574,6 +582,51 @@ void hrt_default_params(hrt_run_params* p) {
     p->watchdog_ms = 0.0;
 }
 
+// Quadrature of the SED bins for raytracing (Sect. 2.6.3): each bin (log-spaced in wavelength) is
+// cut at the nodes of the emission pdf and of the extinction; 3-point Gauss-Legendre in nu on each
+// piece; chi log-log between the dust nodes in FP64.  off[b]..off[b+1] are the nodes of bin b.
+static void rt_quadrature(const hrt_ctx* ctx, const std::vector<double>& pnodes, std::vector<int32_t>& off,
+                          std::vector<int32_t>& jv, std::vector<int32_t>& bin, std::vector<float>& wv,
+                          std::vector<float>& chiv) {
+    const int nsed = ctx->nsed;
+    const double lmin = ctx->lam_min_um * 1e-4, lmax = ctx->lam_max_um * 1e-4;
+    std::vector<double> brk(pnodes);
+    brk.insert(brk.end(), ctx->nu.begin(), ctx->nu.end());
+    std::sort(brk.begin(), brk.end());
+    brk.erase(std::unique(brk.begin(), brk.end()), brk.end());
+    const double gx[3] = {-std::sqrt(0.6), 0.0, std::sqrt(0.6)}, gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    const int nn = (int)ctx->nu.size(), np = (int)pnodes.size();
+    off.assign(nsed + 1, 0);
+    jv.clear(); bin.clear(); wv.clear(); chiv.clear();
+    for (int b = 0; b < nsed; ++b) {
+        const double nu_lo = C_LIGHT_CGS / (lmin * std::pow(lmax / lmin, (double)(b + 1) / nsed));
+        const double nu_hi = C_LIGHT_CGS / (lmin * std::pow(lmax / lmin, (double)b / nsed));
+        off[b] = (int32_t)wv.size();
+        std::vector<double> cuts{nu_lo};
+        for (double x : brk)
+            if (x > nu_lo && x < nu_hi) cuts.push_back(x);
+        cuts.push_back(nu_hi);
+        for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+            const double mid = 0.5 * (cuts[c] + cuts[c + 1]), half = 0.5 * (cuts[c + 1] - cuts[c]);
+            for (int g = 0; g < 3; ++g) {
+                const double x = mid + half * gx[g];
+                int j = (int)(std::upper_bound(pnodes.begin(), pnodes.end(), x) - pnodes.begin()) - 1;
+                j = std::min(std::max(j, 0), np - 2);
+                int k = (int)(std::upper_bound(ctx->nu.begin(), ctx->nu.end(), x) - ctx->nu.begin()) - 1;
+                k = std::min(std::max(k, 0), nn - 2);
+                double t = std::log(x / ctx->nu[k]) / std::log(ctx->nu[k + 1] / ctx->nu[k]);
+                t = std::min(std::max(t, 0.0), 1.0);
+                const double chi = std::exp((1 - t) * std::log(ctx->chi[k]) + t * std::log(ctx->chi[k + 1]));
+                jv.push_back(j);
+                bin.push_back(b);
+                wv.push_back((float)(half * gw[g]));
+                chiv.push_back((float)chi);
+            }
+        }
+    }
+    off[nsed] = (int32_t)wv.size();
+}
+
 int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* params, hrt_iter_stats* out) {
     if (!ctx) return HRT_EINVAL;
     hrt_run_params P;
@@ -584,6 +637,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (P.max_interactions < 0) return ctx->fail(HRT_EINVAL, "max_interactions < 0");
     if (P.pda_min_visits < 0 || P.pda_min_visits > 0xFFFFFFFFll)
         return ctx->fail(HRT_EINVAL, "pda_min_visits must be in [0, 2^32)");
+    if (P.raytrace_rays < 0 || P.raytrace_rays > 0xFFFFFFFFll)
+        return ctx->fail(HRT_EINVAL, "raytrace_rays must be in [0, 2^32)");
     const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
     if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
         return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");
@@ -644,6 +699,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     A.epsL0 = A.eps * ctx->L0;
     A.max_interactions = P.max_interactions;
     A.peel = P.peel && ctx->nobs > 0;
+    const bool raytrace = A.peel && !P.update_temperature && P.raytrace_rays > 0;
+    A.rt = raytrace ? 1 : 0;
     A.terminate_on_absorb = P.terminate_on_absorb;
     A.budget_ns = P.watchdog_ms > 0 ? (uint64_t)(P.watchdog_ms * 1e6) : 0ull;
     A.smem_sed = (size_t)ctx->obs.nobs * ctx->obs.nsed * 8 + (size_t)N_ESC_MU * ctx->obs.nsed * 4 <= 96 * 1024;
@@ -673,6 +730,74 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
                                                  : launch_propagate_event(job, L, s, &launched);
     CK(e, "propagate");
     CK(cudaEventRecord(ctx->ev[1], s), "event");
+    if (raytrace) {
+        std::vector<int32_t> qd_off, qd_j, qd_bin, qs_off, qs_j, qs_bin;
+        std::vector<float> qd_w, qd_chi, qs_w, qs_chi;
+        rt_quadrature(ctx, ctx->nu, qd_off, qd_j, qd_bin, qd_w, qd_chi);
+        std::vector<double> snu(NSPEC);
+        const double a0 = ctx->nu.front(), a1 = ctx->nu.back();
+        for (int k = 0; k < NSPEC; ++k) snu[k] = a0 * std::pow(a1 / a0, (double)k / (NSPEC - 1));
+        snu.front() = a0;
+        snu.back() = a1;
+        rt_quadrature(ctx, snu, qs_off, qs_j, qs_bin, qs_w, qs_chi);
+        std::vector<float> inv(ctx->nu.size());
+        for (size_t k = 0; k + 1 < ctx->nu.size(); ++k) inv[k] = (float)(1.0 / (ctx->nu[k + 1] - ctx->nu[k]));
+        const int npt = (int)ctx->pts.size();
+        std::vector<double> Ls(std::max(npt, 1), 0.0);
+        for (int i = 0; i < npt; ++i) Ls[i] = ctx->pts[i].L;
+        CK(ctx->d_rt_qd_off.upload(qd_off.data(), qd_off.size(), s), "raytrace");
+        CK(ctx->d_rt_qd_j.upload(qd_j.data(), qd_j.size(), s), "raytrace");
+        CK(ctx->d_rt_qd_bin.upload(qd_bin.data(), qd_bin.size(), s), "raytrace");
+        CK(ctx->d_rt_qd_w.upload(qd_w.data(), qd_w.size(), s), "raytrace");
+        CK(ctx->d_rt_qd_chi.upload(qd_chi.data(), qd_chi.size(), s), "raytrace");
+        CK(ctx->d_rt_qs_off.upload(qs_off.data(), qs_off.size(), s), "raytrace");
+        CK(ctx->d_rt_qs_j.upload(qs_j.data(), qs_j.size(), s), "raytrace");
+        CK(ctx->d_rt_qs_bin.upload(qs_bin.data(), qs_bin.size(), s), "raytrace");
+        CK(ctx->d_rt_qs_w.upload(qs_w.data(), qs_w.size(), s), "raytrace");
+        CK(ctx->d_rt_qs_chi.upload(qs_chi.data(), qs_chi.size(), s), "raytrace");
+        CK(ctx->d_rt_inv_dnu.upload(inv.data(), inv.size(), s), "raytrace");
+        CK(ctx->d_src_L.upload(Ls.data(), Ls.size(), s), "raytrace");
+        CK(ctx->d_rt_cdf.alloc(nc), "raytrace");
+        CK(ctx->d_rt_sums.alloc(nc / 1024 + 2), "raytrace");
+        CK(ctx->d_rt_total.alloc(1), "raytrace");
+        CK(ctx->d_rt_col.alloc((size_t)P.raytrace_rays * ctx->nobs), "raytrace");
+        CK(ctx->d_rt_row.alloc((size_t)P.raytrace_rays), "raytrace");
+        RtJob J;
+        std::memset(&J, 0, sizeof(J));
+        J.n1 = ctx->n[0]; J.n2 = ctx->n[1]; J.n3 = ctx->n[2];
+        J.nc = nc;
+        J.rho = ctx->d_rho.p;
+        J.va = ctx->d_va.p; J.vb = ctx->d_vb.p; J.vc = ctx->d_vc.p;
+        J.T = ctx->d_T.p;
+        J.lnT = ctx->d_lnT.p; J.lnE = ctx->d_lnE.p;
+        J.nT = (int)ctx->Tn.size();
+        J.nnu = (int)ctx->nu.size();
+        J.emit_row = ctx->d_row.p;
+        J.cdf_emit = ctx->d_cdf_emit.p;
+        J.inv_dnu = ctx->d_rt_inv_dnu.p;
+        J.qd_off = ctx->d_rt_qd_off.p; J.qd_j = ctx->d_rt_qd_j.p; J.qd_bin = ctx->d_rt_qd_bin.p;
+        J.qd_w = ctx->d_rt_qd_w.p; J.qd_chi = ctx->d_rt_qd_chi.p; J.nqd = (int)qd_w.size();
+        J.qs_off = ctx->d_rt_qs_off.p; J.qs_j = ctx->d_rt_qs_j.p; J.qs_bin = ctx->d_rt_qs_bin.p;
+        J.qs_w = ctx->d_rt_qs_w.p; J.qs_chi = ctx->d_rt_qs_chi.p; J.nqs = (int)qs_w.size();
+        J.nsed = ctx->nsed;
+        J.npoint = npt;
+        J.src_col = job.src.col;
+        J.src_pos = ctx->d_src_pos.p;
+        J.src_L = ctx->d_src_L.p;
+        J.spec_cdf = ctx->d_spec_cdf.p;
+        J.spec_nu = ctx->d_spec_nud.p;
+        J.nspec = NSPEC;
+        J.n_rays = P.raytrace_rays;
+        J.key0 = A.key0; J.key1 = A.key1;
+        J.iter_key = 0x40000000u | (uint32_t)ctx->iteration;
+        J.model_key = A.model_key;
+        J.cdf = ctx->d_rt_cdf.p; J.scan_sums = ctx->d_rt_sums.p; J.total = ctx->d_rt_total.p;
+        J.col = ctx->d_rt_col.p; J.row = ctx->d_rt_row.p;
+        J.sed = ctx->d_sed.p; J.img = ctx->d_img.p;
+        J.counters = ctx->d_counters.p;
+        double Ldust = 0.0;
+        CK(run_raytrace(ctx->grid, ctx->obs, J, &Ldust, s, &launched), "raytrace");
+    }
     const int64_t k_rank = ctx->n_dust > 0 ? (nc - ctx->n_dust) + (int64_t)std::ceil(P.p * (double)ctx->n_dust) - 1 : 0;
     PdaStats pda_stats{0, 0, 0.0};
     if (P.update_temperature) {

@@ -112,6 +112,10 @@ struct hrt_ctx {
     DBuf<unsigned long long> d_pda_count;
     DBuf<int> d_pda_flag;
     bool visits_valid = false;
+    // ---- raytracing (Sect. 2.6.3)
+    DBuf<float> d_rho, d_rt_qd_w, d_rt_qd_chi, d_rt_qs_w, d_rt_qs_chi, d_rt_inv_dnu, d_rt_col;
+    DBuf<int32_t> d_rt_qd_off, d_rt_qd_j, d_rt_qd_bin, d_rt_qs_off, d_rt_qs_j, d_rt_qs_bin, d_rt_row;
+    DBuf<double> d_rt_cdf, d_rt_sums, d_rt_total, d_src_L;
     unsigned long long* h_stats = nullptr;   // pinned: counters, clamps, Q key
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // start, after propagation, end, before propagation
     double Q_prev = std::numeric_limits<double>::infinity();

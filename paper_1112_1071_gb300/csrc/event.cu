@@ -97,7 +97,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     // emission from a point source with precomputed columns needs no walk
     auto start_peel = [&](int ob) {
         if (prelocate && s.col) {
-            tau = pk.dust.chi * __ldg(s.col + (int64_t)pk.src * o.nobs + ob);
+            tau = pk.dust.chi * fmaxf(__ldg(s.col + (int64_t)pk.src * o.nobs + ob), 0.f);
             mode = M_PEEL_DONE;
             return;
         }
@@ -111,9 +111,10 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         if (prelocate && !grid_locate<G>(g, pk.r)) mode = M_PEEL_DONE;
     };
     // after an emission or interaction: peel (if wanted) then draw a new optical depth
-    auto after_event = [&](int kind, int relocate) {
+    // raytraced: point-source emission or re-emission, which an a.rt pass raytraces instead
+    auto after_event = [&](int kind, int relocate, bool raytraced) {
         if constexpr (PEEL) {
-            if (a.peel && pk.sbin >= 0 && o.nobs > 0) {
+            if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !(raytraced && a.rt)) {
                 saved = pk.r;
                 pkind = kind;
                 prelocate = relocate;
@@ -211,7 +212,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                         const int row = min(max(__ldg(d.emit_row + pk.r.ci), 0), d.nT - 1);   // bounds check
                         set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
                         porg = pk.r.p;
-                        after_event(PEEL_ISO, 0);
+                        after_event(PEEL_ISO, 0, true);
                     }
                 } else {
                     lc.v[C_SCATTER]++;
@@ -220,7 +221,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     uin = pk.r.u;
                     set_dir(pk.r, scatter_dir(uin, mu, u2));
                     porg = pk.r.p;
-                    after_event(PEEL_HG, 0);
+                    after_event(PEEL_HG, 0, false);
                 }
             }
         } else if (PEEL && mode == M_PEEL_DONE) {
@@ -240,7 +241,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     lc.v[C_PACKETS_DONE]++;
                 } else {
                     porg = pk.last_origin;
-                    after_event(PEEL_ISO, pk.emit_relocate);
+                    after_event(PEEL_ISO, pk.emit_relocate, pk.src < s.npoint);
                 }
             }
         }

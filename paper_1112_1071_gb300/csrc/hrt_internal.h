@@ -107,6 +107,48 @@ struct PdaJob {
     unsigned long long* count;
     int* flag;
 };
+// raytrace.cu: raytracing of point-source and dust emission (Sect. 2.6.3)
+struct RtJob {
+    int32_t n1, n2, n3;
+    int64_t nc;
+    const float* rho;                        // g/cm^3
+    const double *va, *vb, *vc;              // per-axis volume factors (cm^3)
+    const double* T;
+    const double *lnT, *lnE;                 // [nT]
+    int32_t nT, nnu;
+    const int32_t* emit_row;                 // re-emission rows of this pass
+    const float* cdf_emit;                   // [nT][nnu]
+    const float* inv_dnu;                    // [nnu-1] 1 / (nu_{j+1} - nu_j)
+    // quadrature of the SED bins: dust rows (qd_*) and source spectra (qs_*), sorted by bin
+    const int32_t *qd_off, *qd_j, *qd_bin;
+    const float *qd_w, *qd_chi;
+    int32_t nqd;
+    const int32_t *qs_off, *qs_j, *qs_bin;
+    const float *qs_w, *qs_chi;
+    int32_t nqs;
+    int32_t nsed, npoint;
+    const float* src_col;                    // [npoint][nobs], -1 outside the grid
+    const float* src_pos;                    // [npoint][3] scaled
+    const double* src_L;                     // [npoint] erg/s
+    const float* spec_cdf;                   // [nsrc][nspec]
+    const double* spec_nu;                   // [nspec]
+    int32_t nspec;
+    // dust rays
+    int64_t n_rays;
+    uint32_t key0, key1, iter_key, model_key;
+    double* cdf;                             // [nc] emission CDF (work)
+    double* scan_sums;                       // [nc / 1024 + 1]
+    double* total;                           // [1] L_dust
+    float* col;                              // [n_rays][nobs]
+    int32_t* row;                            // [n_rays]
+    double eps4pi;                           // L_dust / n_rays / (4 pi), set by run_raytrace
+    double* sed;
+    double* img;
+    unsigned long long* counters;
+};
+cudaError_t run_raytrace(const DevGrid& g, const DevObs& o, RtJob J, double* host_total, cudaStream_t s,
+                         int* launched);
+
 struct PdaStats {
     int64_t n_cells;
     int64_t iterations;

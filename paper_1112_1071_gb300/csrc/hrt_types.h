@@ -122,6 +122,8 @@ struct RunArgs {
     int64_t max_interactions;
     int32_t peel;
     int32_t terminate_on_absorb;
+    int32_t rt;                    // 1: point-source emission and re-emission are raytraced, not peeled
+    int32_t pad_rt;
     uint64_t budget_ns;            // watchdog budget after the launch stamp, 0 = none
     int32_t regroup;               // event kernel: leave walk phase below this many walkers
     int32_t smem_sed;              // 1: SED tallies in shared memory

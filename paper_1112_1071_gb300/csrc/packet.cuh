@@ -85,7 +85,7 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
         set_dir(pr, n);
         float tau = 0.f;
         bool inside = true;
-        if (col) tau = chi * __ldg(col + ob);
+        if (col) tau = chi * fmaxf(__ldg(col + ob), 0.f);
         else {
             if (relocate) inside = grid_locate<G>(g, pr);
             if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], F_INF);
@@ -105,6 +105,32 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
                 }
             }
         }
+    }
+}
+
+// Cell c and a point uniform in its volume from three uniforms (Cartesian: each coordinate;
+// spherical: r^3, cos(theta) and phi uniform), as for emission from a cell.
+template <int G>
+__device__ __forceinline__ void place_in_cell(const DevGrid& g, int64_t c, float f0, float f1, float f2, Ray& r) {
+    r.i = (int)(c % g.n1);
+    r.j = (int)((c / g.n1) % g.n2);
+    r.k = (int)(c / ((int64_t)g.n1 * g.n2));
+    r.ci = (int32_t)c;
+    if constexpr (G == GRID_CARTESIAN) {
+        const float x0 = __ldg(g.w1 + r.i), y0 = __ldg(g.w2 + r.j), z0 = __ldg(g.w3 + r.k);
+        r.p = make_float3(x0 + f0 * (__ldg(g.w1 + r.i + 1) - x0), y0 + f1 * (__ldg(g.w2 + r.j + 1) - y0),
+                          z0 + f2 * (__ldg(g.w3 + r.k + 1) - z0));
+    } else {
+        const double r0 = __ldg(g.rwd + r.i), r1 = __ldg(g.rwd + r.i + 1);
+        const double rad = cbrt(r0 * r0 * r0 + (double)f0 * (r1 * r1 * r1 - r0 * r0 * r0));
+        const double c0 = __ldg(g.cthd + r.j), c1 = __ldg(g.cthd + r.j + 1);
+        const double ct = c0 + (double)f1 * (c1 - c0);
+        const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        const float ph0 = __ldg(g.phw + r.k);
+        const float ph = ph0 + f2 * (__ldg(g.phw + r.k + 1) - ph0);
+        float sp, cp;
+        sincosf(ph, &sp, &cp);
+        r.p = make_float3((float)(rad * st) * cp, (float)(rad * st) * sp, (float)(rad * ct));
     }
 }
 
@@ -128,33 +154,14 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
         pk.last_origin = at.p;
         pk.emit_relocate = 1;
         if (!grid_locate<G>(g, pk.r)) return false;
-        if (a.peel && inline_peel)
+        if (a.peel && !a.rt && inline_peel)     // raytraced instead when a.rt (Sect. 2.6.3)
             peel_event<G>(g, d, o, a, t, sed_s, at, pk.r.u, PEEL_ISO, true, pk.dust.chi, pk.sbin, lc,
                           s.col ? s.col + (int64_t)src * o.nobs : nullptr);
     } else {
         pk.emit_relocate = 0;
         const int64_t c = select_cdf<double>(s.cell_cdf, g.ncells, (double)pk.rng.next());
-        pk.r.i = (int)(c % g.n1);
-        pk.r.j = (int)((c / g.n1) % g.n2);
-        pk.r.k = (int)(c / ((int64_t)g.n1 * g.n2));
-        pk.r.ci = (int32_t)c;
         const float f0 = pk.rng.next(), f1 = pk.rng.next(), f2 = pk.rng.next();
-        if constexpr (G == GRID_CARTESIAN) {
-            const float x0 = __ldg(g.w1 + pk.r.i), y0 = __ldg(g.w2 + pk.r.j), z0 = __ldg(g.w3 + pk.r.k);
-            pk.r.p = make_float3(x0 + f0 * (__ldg(g.w1 + pk.r.i + 1) - x0), y0 + f1 * (__ldg(g.w2 + pk.r.j + 1) - y0),
-                                 z0 + f2 * (__ldg(g.w3 + pk.r.k + 1) - z0));
-        } else {
-            const double r0 = __ldg(g.rwd + pk.r.i), r1 = __ldg(g.rwd + pk.r.i + 1);
-            const double rad = cbrt(r0 * r0 * r0 + (double)f0 * (r1 * r1 * r1 - r0 * r0 * r0));
-            const double c0 = __ldg(g.cthd + pk.r.j), c1 = __ldg(g.cthd + pk.r.j + 1);
-            const double ct = c0 + (double)f1 * (c1 - c0);
-            const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-            const float ph0 = __ldg(g.phw + pk.r.k);
-            const float ph = ph0 + f2 * (__ldg(g.phw + pk.r.k + 1) - ph0);
-            float sp, cp;
-            sincosf(ph, &sp, &cp);
-            pk.r.p = make_float3((float)(rad * st) * cp, (float)(rad * st) * sp, (float)(rad * ct));
-        }
+        place_in_cell<G>(g, c, f0, f1, f2, pk.r);
         const float u1 = pk.rng.next(), u2 = pk.rng.next();
         set_dir(pk.r, isotropic_dir(u1, u2));
         set_frequency(pk, d, o, sample_table(s.spec_nu, s.spec_cdf + (int64_t)src * s.nspec, s.nspec, pk.rng.next()));
@@ -182,7 +189,7 @@ __device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, con
         set_dir(pk.r, isotropic_dir(u1, u2));
         const int row = min(max(__ldg(d.emit_row + pk.r.ci), 0), d.nT - 1);   // bounds check
         set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
-        if (a.peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
+        if (a.peel && !a.rt) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
     } else {
         lc.v[C_SCATTER]++;
         const float mu = hg_mu(d.g, pk.rng.next());

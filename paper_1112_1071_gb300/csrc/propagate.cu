@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
     flush_shared(o, a, t, st);
 }
 
-// Columns sum rhoL l from each point source to the grid edge along each observer direction: the
+// Columns sum rhoL l from each point source to the grid edge along each observer direction (-1
+// for a source outside the grid, which emits no packets into it): the
 // peel-off rays of every packet emitted by a point source start at the source and run along the
 // observer direction, so their optical depth is chi(nu) times this column (Sect. 2.6.2).
 template <int G>
@@ -112,7 +113,7 @@ __global__ void k_source_columns(DevGrid g, DevSources s, DevObs o, float* col) 
     Ray r;
     r.p = make_float3(s.pos[3 * src], s.pos[3 * src + 1], s.pos[3 * src + 2]);
     set_dir(r, make_float3(o.n[3 * ob], o.n[3 * ob + 1], o.n[3 * ob + 2]));
-    float sum = 0.f;
+    float sum = -1.f;                  // -1: the source lies outside the grid
     unsigned long long ncross = 0;
     if (grid_locate<G>(g, r)) sum = tau_to_edge<G>(g, r, 1.f, ncross, F_INF);
     col[q] = sum;
