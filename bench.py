@@ -46,6 +46,10 @@ UNIT = "packets/s"
 B_CROSS = 20.0
 B_PEEL = 4.0
 B_REEMIT = 400.0
+# DRAM bytes (read + write) per propagation launch from ncu on the current kernel, averaged over
+# a step's launch mix (profiles/k_event_flared_disk_launches.md); the first touch of the
+# resident grid and tables, independent of the packet count
+TRAFFIC_PER_LAUNCH = 0.78e6
 
 
 def parse():
@@ -331,7 +335,8 @@ def main():
             "crossings_per_step": sum(s["n_crossings"] for s in last),
             "peel_crossings_per_step": sum(s["n_peel_crossings"] for s in last),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH if kern == hrt.HRT_KERNEL_EVENT else None,
+                         "traffic_unit": "bytes per launch (ncu)", "peak_source": src,
                          "kernel": "k_event (propagation)" if kern == hrt.HRT_KERNEL_EVENT else "k_plain",
                          "kernel_ms_per_step": kms, "algorithmic_bytes_per_step": byts},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rho_h.numel() * 4 + T0_h.numel() * 8),
