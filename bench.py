@@ -46,9 +46,9 @@ UNIT = "packets/s"
 B_CROSS = 20.0
 B_PEEL = 4.0
 B_REEMIT = 400.0
-# DRAM bytes (read + write) per propagation launch from ncu on the current kernel, averaged over
-# a step's launch mix (profiles/k_event_flared_disk_launches.md); the first touch of the
-# resident grid and tables, independent of the packet count
+# DRAM bytes (read + write) per propagation launch from an ncu capture of the current kernel on
+# a small case of this workload, averaged over a step's launch mix (10 Lucy, 1 imaging): the
+# first touch of the resident grid and tables, which does not grow with the packet count
 TRAFFIC_PER_LAUNCH = 0.78e6
 
 
