@@ -88,7 +88,8 @@ double or_uniform_from_word(uint32_t x) { return ((double)(x >> 8) + 1.0) * (1.0
 
 /* ------------------------------------------------------------------ model description */
 typedef struct {
-    int32_t gtype;            /* 0 cartesian (x,y,z); 1 spherical-polar (r, theta, phi) */
+    int32_t gtype;            /* 0 cartesian (x,y,z); 1 spherical-polar (r, theta, phi);
+                                 2 cylindrical-polar (R, z, phi) */
     int32_t n[3];             /* cells per axis */
     const double* w[3];       /* walls per axis: cm, or rad for theta and phi */
     const double* rho;        /* [n3][n2][n1] g/cm^3 */
@@ -121,6 +122,12 @@ typedef struct {
     int32_t img_nx, img_ny, nimg;
     double img_half;          /* cm */
     const int32_t* img_bin;   /* [nimg] SED bin of each image wavelength */
+    /* external isotropic sources (after the point sources in the source list, before a cell
+     * source): spheres of centre ext_c and radius ext_R emitting inwards */
+    int32_t next;
+    const double* ext_c;      /* [next][3] cm */
+    const double* ext_R;      /* [next] cm */
+    double L0;                /* grid scale (cm): the entry nudge of external packets is 1e-6 L0 */
 } or_model;
 
 typedef struct {
@@ -468,6 +475,99 @@ static void sph_cross_hole(const or_model* m, double p[3], const double u[3], in
     c[2] = cc3[2];
 }
 
+/* ------------------------------------------------------------------ cylindrical-polar grid */
+/* Walls: cylinders R_i about the z axis (R_0 > 0: an inner vacuum hole), planes z_j and
+ * half-planes phi_k.  Index order [phi][z][R]. */
+static int cyl_locate(const or_model* m, const double p[3], const double u[3], int c[3]) {
+    const double* Rw = m->w[0];
+    double R = sqrt(p[0] * p[0] + p[1] * p[1]);
+    double vR = p[0] * u[0] + p[1] * u[1];
+    int j = locate_axis(m->w[1], m->n[1], p[2], u[2]);
+    if (j < 0) return -1;
+    c[1] = j;
+    double ph, vp;
+    if (R == 0.0) { ph = wrap_phi(atan2(u[1], u[0])); vp = 0.0; }
+    else { ph = wrap_phi(atan2(p[1], p[0])); vp = dphids(p, u); }
+    int k;
+    if (m->n[2] == 1) k = 0;
+    else if (ph == 0.0 && !(vp > 0)) k = m->n[2] - 1;
+    else {
+        k = locate_axis(m->w[2], m->n[2], ph, vp);
+        if (k < 0) k = m->n[2] - 1;
+    }
+    c[2] = k;
+    if (R < Rw[0] || (R == Rw[0] && Rw[0] > 0 && !(vR > 0))) { c[0] = -1; return 1; }
+    int i = locate_axis(Rw, m->n[0], R, vR);
+    if (i < 0) return -1;
+    c[0] = i;
+    return 0;
+}
+
+static double cyl_exit(const or_model* m, const double p[3], const double u[3], const int c[3],
+                       int* axis, int* dir) {
+    const double* Rw = m->w[0];
+    const double* zw = m->w[1];
+    const double* pw = m->w[2];
+    double a = u[0] * u[0] + u[1] * u[1];
+    double b = p[0] * u[0] + p[1] * u[1];
+    double R2 = p[0] * p[0] + p[1] * p[1];
+    double tol = 1e-9 * Rw[m->n[0]];
+    double best = INFINITY;
+    *axis = -1;
+    *dir = 0;
+    if (a > 0) {
+        /* outer cylinder: the far root, always ahead of a point inside (a s^2 + 2 b s + cc = 0) */
+        double cc = R2 - Rw[c[0] + 1] * Rw[c[0] + 1];
+        double sq = sqrt(fmax(b * b - a * cc, 0.0));
+        double s = b > 0 ? -cc / (b + sq) : (-b + sq) / a;
+        best = fmax(s, 0.0);
+        *axis = 0;
+        *dir = 1;
+        /* inner cylinder, entered only while moving inwards */
+        if (Rw[c[0]] > 0 && b < 0) {
+            double ci = R2 - Rw[c[0]] * Rw[c[0]];
+            double disc = b * b - a * ci;
+            if (disc >= 0) {
+                double si = fmax(ci / (-b + sqrt(disc)), 0.0);
+                if (si < best) { best = si; *dir = -1; }
+            }
+        }
+    }
+    /* z planes */
+    if (u[2] != 0) {
+        double s = u[2] > 0 ? (zw[c[1] + 1] - p[2]) / u[2] : (zw[c[1]] - p[2]) / u[2];
+        s = fmax(s, 0.0);
+        if (s < best) { best = s; *axis = 1; *dir = u[2] > 0 ? 1 : -1; }
+    }
+    if (m->n[2] > 1) {
+        double s = phi_root(p, u, pw[c[2]], -1, tol);
+        if (s < best) { best = s; *axis = 2; *dir = -1; }
+        s = phi_root(p, u, pw[c[2] + 1], +1, tol);
+        if (s < best) { best = s; *axis = 2; *dir = 1; }
+    }
+    return best;
+}
+
+/* Cross the inner vacuum cylinder to its far side; returns 1 when the ray leaves the grid
+ * through a z plane on the way (or runs along the axis), 0 with c set in the shell R_0. */
+static int cyl_cross_hole(const or_model* m, double p[3], const double u[3], int c[3]) {
+    double a = u[0] * u[0] + u[1] * u[1];
+    if (!(a > 0)) return 1;
+    double R0 = m->w[0][0];
+    double b = p[0] * u[0] + p[1] * u[1];
+    double cc = p[0] * p[0] + p[1] * p[1] - R0 * R0;
+    double sq = sqrt(fmax(b * b - a * cc, 0.0));
+    double s = b > 0 ? -cc / (b + sq) : (-b + sq) / a;
+    if (s < 0) s = 0;
+    for (int q = 0; q < 3; ++q) p[q] += s * u[q];
+    int c3[3];
+    if (cyl_locate(m, p, u, c3) < 0) return 1;
+    c[0] = 0;
+    c[1] = c3[1];
+    c[2] = c3[2];
+    return 0;
+}
+
 /* ------------------------------------------------------------------ generic grid API */
 /* 0 inside, -1 outside.  Spherical points in the hole are moved through it. */
 static int grid_locate(const or_model* m, double p[3], const double u[3], int c[3]) {
@@ -476,6 +576,12 @@ static int grid_locate(const or_model* m, double p[3], const double u[3], int c[
             c[a] = locate_axis(m->w[a], m->n[a], p[a], u[a]);
             if (c[a] < 0) return -1;
         }
+        return 0;
+    }
+    if (m->gtype == 2) {
+        int st = cyl_locate(m, p, u, c);
+        if (st < 0) return -1;
+        if (st == 1 && cyl_cross_hole(m, p, u, c)) return -1;
         return 0;
     }
     int st = sph_locate(m, p, u, c);
@@ -496,6 +602,7 @@ static int grid_locate(const or_model* m, double p[3], const double u[3], int c[
 
 static double grid_exit(const or_model* m, const double p[3], const double u[3], const int c[3],
                         int* axis, int* dir) {
+    if (m->gtype == 2) return cyl_exit(m, p, u, c, axis, dir);
     return m->gtype == 0 ? cart_exit(m, p, u, c, axis, dir) : sph_exit(m, p, u, c, axis, dir);
 }
 
@@ -503,6 +610,17 @@ static double grid_exit(const or_model* m, const double p[3], const double u[3],
 static int grid_step(const or_model* m, double p[3], const double u[3], int c[3], int axis, int dir) {
     c[axis] += dir;
     if (m->gtype == 0) return (c[axis] < 0 || c[axis] >= m->n[axis]) ? 1 : 0;
+    if (m->gtype == 2) {
+        if (axis == 0) {
+            if (c[0] >= m->n[0]) return 1;
+            if (c[0] < 0) return cyl_cross_hole(m, p, u, c);
+            return 0;
+        }
+        if (axis == 1) return (c[1] < 0 || c[1] >= m->n[1]) ? 1 : 0;
+        if (c[2] < 0) c[2] += m->n[2];
+        if (c[2] >= m->n[2]) c[2] -= m->n[2];
+        return 0;
+    }
     if (axis == 0) {
         if (c[0] >= m->n[0]) return 1;
         if (c[0] < 0) sph_cross_hole(m, p, u, c);
@@ -660,6 +778,79 @@ static void peel(const or_model* m, const double p[3], const int c[3], const dou
     }
 }
 
+/* A point uniform in the volume of cell c from three uniforms (Cartesian: each coordinate;
+ * spherical: r^3, cos(theta), phi uniform; cylindrical: R^2, z, phi uniform). */
+static void place_in_cell(const or_model* m, const int c[3], double f0, double f1, double f2, double p[3]) {
+    if (m->gtype == 0) {
+        double f[3] = {f0, f1, f2};
+        for (int a = 0; a < 3; ++a) p[a] = m->w[a][c[a]] + f[a] * (m->w[a][c[a] + 1] - m->w[a][c[a]]);
+    } else if (m->gtype == 1) {
+        double r0 = m->w[0][c[0]], r1 = m->w[0][c[0] + 1];
+        double r = cbrt(r0 * r0 * r0 + f0 * (r1 * r1 * r1 - r0 * r0 * r0));
+        double ct0 = cos(m->w[1][c[1]]), ct1 = cos(m->w[1][c[1] + 1]);
+        double ct = ct0 + f1 * (ct1 - ct0);
+        double ph = m->w[2][c[2]] + f2 * (m->w[2][c[2] + 1] - m->w[2][c[2]]);
+        double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        p[0] = r * st * cos(ph); p[1] = r * st * sin(ph); p[2] = r * ct;
+    } else {
+        double R0 = m->w[0][c[0]], R1 = m->w[0][c[0] + 1];
+        double R = sqrt(R0 * R0 + f0 * (R1 * R1 - R0 * R0));
+        double z = m->w[1][c[1]] + f1 * (m->w[1][c[1] + 1] - m->w[1][c[1]]);
+        double ph = m->w[2][c[2]] + f2 * (m->w[2][c[2] + 1] - m->w[2][c[2]]);
+        p[0] = R * cos(ph); p[1] = R * sin(ph); p[2] = z;
+    }
+}
+
+/* Parameter t >= 0 at which the ray p + t u first enters the grid's outer boundary (0 when p is
+ * already inside), or -1 when it misses the grid. */
+static double grid_entry(const or_model* m, const double p[3], const double u[3]) {
+    double tmin = -INFINITY, tmax = INFINITY;
+    if (m->gtype == 1) {
+        double ro = m->w[0][m->n[0]];
+        double b = dot3(p, u), c = dot3(p, p) - ro * ro;
+        if (c <= 0) return 0.0;
+        double disc = b * b - c;
+        if (disc < 0 || b >= 0) return -1.0;
+        return c / (-b + sqrt(disc));
+    }
+    if (m->gtype == 0) {
+        for (int a = 0; a < 3; ++a) {
+            double lo = m->w[a][0], hi = m->w[a][m->n[a]];
+            if (u[a] == 0) {
+                if (p[a] < lo || p[a] > hi) return -1.0;
+                continue;
+            }
+            double t1 = (lo - p[a]) / u[a], t2 = (hi - p[a]) / u[a];
+            tmin = fmax(tmin, fmin(t1, t2));
+            tmax = fmin(tmax, fmax(t1, t2));
+        }
+    } else {
+        double Ro = m->w[0][m->n[0]];
+        double a = u[0] * u[0] + u[1] * u[1];
+        double b = p[0] * u[0] + p[1] * u[1];
+        double c = p[0] * p[0] + p[1] * p[1] - Ro * Ro;
+        if (a == 0) {
+            if (c > 0) return -1.0;
+        } else {
+            double disc = b * b - a * c;
+            if (disc < 0) return -1.0;
+            double sq = sqrt(disc);
+            tmin = (-b - sq) / a;
+            tmax = (-b + sq) / a;
+        }
+        double lo = m->w[1][0], hi = m->w[1][m->n[1]];
+        if (u[2] == 0) {
+            if (p[2] < lo || p[2] > hi) return -1.0;
+        } else {
+            double t1 = (lo - p[2]) / u[2], t2 = (hi - p[2]) / u[2];
+            tmin = fmax(tmin, fmin(t1, t2));
+            tmax = fmin(tmax, fmax(t1, t2));
+        }
+    }
+    if (tmax < fmax(tmin, 0.0)) return -1.0;
+    return fmax(tmin, 0.0);
+}
+
 /* ------------------------------------------------------------------ raytracing (Sect. 2.6.3) */
 /* Dust-emission rays: ray k draws from its own Philox stream (key, counter (draw/4, k, iter_key,
  * model)): u0 picks the cell from the cumulative emitted luminosity cdf_L (smallest index with
@@ -682,18 +873,7 @@ int or_raytrace_rays(const or_model* m, const or_params* P, int64_t n_rays, cons
         c[2] = (int)(ci / ((int64_t)m->n[0] * m->n[1]));
         double f0 = uniform(&rng), f1 = uniform(&rng), f2 = uniform(&rng);
         double p[3];
-        if (m->gtype == 0) {
-            double f[3] = {f0, f1, f2};
-            for (int a = 0; a < 3; ++a) p[a] = m->w[a][c[a]] + f[a] * (m->w[a][c[a] + 1] - m->w[a][c[a]]);
-        } else {
-            double r0 = m->w[0][c[0]], r1 = m->w[0][c[0] + 1];
-            double r = cbrt(r0 * r0 * r0 + f0 * (r1 * r1 * r1 - r0 * r0 * r0));
-            double ct0 = cos(m->w[1][c[1]]), ct1 = cos(m->w[1][c[1] + 1]);
-            double ct = ct0 + f1 * (ct1 - ct0);
-            double ph = m->w[2][c[2]] + f2 * (m->w[2][c[2] + 1] - m->w[2][c[2]]);
-            double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-            p[0] = r * st * cos(ph); p[1] = r * st * sin(ph); p[2] = r * ct;
-        }
+        place_in_cell(m, c, f0, f1, f2, p);
         cells[k] = ci;
         for (int a = 0; a < 3; ++a) pos[3 * k + a] = p[a];
         for (int o = 0; o < m->nobs; ++o) {
@@ -729,24 +909,40 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
         double p0[3] = {p[0], p[1], p[2]};
         if (grid_locate(m, p, u, c) < 0) { R->e_escaped += eps; return; }
         if (P->peel && !P->raytrace) peel(m, p0, c, u, nu, eps, PEEL_EMIT, R);
+    } else if (s < m->npoint + m->next) {
+        /* external isotropic source (Sect. 2.1.1): a point uniform on the sphere, a direction
+         * into it with the cosine-weighted (isotropic-intensity) distribution about the inward
+         * normal, cos = sqrt(u), in the fixed frame of the normal; no peel-off (background) */
+        int e = s - m->npoint;
+        double nh[3], u1 = uniform(&rng), u2 = uniform(&rng);
+        or_isotropic(u1, u2, nh);
+        for (int a = 0; a < 3; ++a) p[a] = m->ext_c[3 * e + a] + m->ext_R[e] * nh[a];
+        double u3 = uniform(&rng), u4 = uniform(&rng);
+        double e1[3], e2[3];
+        if (fabs(nh[2]) < 0.99999) { e1[0] = -nh[1]; e1[1] = nh[0]; e1[2] = 0.0; }
+        else { e1[0] = nh[2]; e1[1] = 0.0; e1[2] = -nh[0]; }
+        double n1 = sqrt(dot3(e1, e1));
+        for (int a = 0; a < 3; ++a) e1[a] /= n1;
+        e2[0] = nh[1] * e1[2] - nh[2] * e1[1];
+        e2[1] = nh[2] * e1[0] - nh[0] * e1[2];
+        e2[2] = nh[0] * e1[1] - nh[1] * e1[0];
+        double ct = sqrt(u3), st = sqrt(1.0 - u3), cp = cos(2.0 * OR_PI * u4), sp = sin(2.0 * OR_PI * u4);
+        for (int a = 0; a < 3; ++a) u[a] = -ct * nh[a] + st * (cp * e1[a] + sp * e2[a]);
+        double un = sqrt(dot3(u, u));
+        for (int a = 0; a < 3; ++a) u[a] /= un;
+        nu = or_sample_table(m->nspec, m->spec_nu, m->spec_cdf + (int64_t)s * m->nspec, uniform(&rng));
+        /* travel through vacuum to the grid; a packet that misses it escapes */
+        double t = grid_entry(m, p, u);
+        if (t < 0) { R->e_escaped += eps; return; }
+        for (int a = 0; a < 3; ++a) p[a] += (t + 1e-6 * m->L0) * u[a];
+        if (grid_locate(m, p, u, c) < 0) { R->e_escaped += eps; return; }
     } else {
         int64_t ci = select_cdf(ncells(m), m->cell_cdf, uniform(&rng));
         c[0] = (int)(ci % m->n[0]);
         c[1] = (int)((ci / m->n[0]) % m->n[1]);
         c[2] = (int)(ci / ((int64_t)m->n[0] * m->n[1]));
         double f0 = uniform(&rng), f1 = uniform(&rng), f2 = uniform(&rng);
-        if (m->gtype == 0) {
-            double f[3] = {f0, f1, f2};
-            for (int a = 0; a < 3; ++a) p[a] = m->w[a][c[a]] + f[a] * (m->w[a][c[a] + 1] - m->w[a][c[a]]);
-        } else {
-            double r0 = m->w[0][c[0]], r1 = m->w[0][c[0] + 1];
-            double r = cbrt(r0 * r0 * r0 + f0 * (r1 * r1 * r1 - r0 * r0 * r0));
-            double ct0 = cos(m->w[1][c[1]]), ct1 = cos(m->w[1][c[1] + 1]);
-            double ct = ct0 + f1 * (ct1 - ct0);
-            double ph = m->w[2][c[2]] + f2 * (m->w[2][c[2] + 1] - m->w[2][c[2]]);
-            double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-            p[0] = r * st * cos(ph); p[1] = r * st * sin(ph); p[2] = r * ct;
-        }
+        place_in_cell(m, c, f0, f1, f2, p);
         double u1 = uniform(&rng), u2 = uniform(&rng);
         or_isotropic(u1, u2, u);
         nu = or_sample_table(m->nspec, m->spec_nu, m->spec_cdf + (int64_t)s * m->nspec, uniform(&rng));

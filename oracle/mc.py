@@ -67,6 +67,7 @@ class ORModel(C.Structure):
         ("nsed", C.c_int32), ("lam_min", C.c_double), ("lam_max", C.c_double),
         ("img_nx", C.c_int32), ("img_ny", C.c_int32), ("nimg", C.c_int32),
         ("img_half", C.c_double), ("img_bin", _ip),
+        ("next", C.c_int32), ("ext_c", _dp), ("ext_R", _dp), ("L0", C.c_double),
     ]
 
 
@@ -168,7 +169,7 @@ class OracleModel:
 
     def __init__(self, wl, t_init: float = 10.0):
         self.wl = wl
-        self.gtype = 0 if wl.grid_type == "cartesian" else 1
+        self.gtype = {"cartesian": 0, "spherical": 1, "cylindrical": 2}[wl.grid_type]
         self.walls = [np.ascontiguousarray(w, dtype=np.float64) for w in wl.walls]
         self.shape = tuple(len(w) - 1 for w in self.walls)
         self.rho = np.ascontiguousarray(wl.rho, dtype=np.float64).reshape(-1)
@@ -180,10 +181,18 @@ class OracleModel:
         self.albedo = np.ascontiguousarray(wl.albedo, dtype=np.float64)
         self.T_nodes = np.ascontiguousarray(wl.T_nodes, dtype=np.float64)
         self.cdf_emit = np.ascontiguousarray(self.dust.cdf, dtype=np.float64)
-        # sources: point sources, then an optional cell source
-        Ls = [float(s["L"]) for s in wl.sources]
+        # sources: point sources, external isotropic sources, then an optional cell source
+        ext = list(getattr(wl, "external_sources", []) or [])
+        Ls = [float(s["L"]) for s in wl.sources] + [float(e["L"]) for e in ext]
         self.src_pos = np.ascontiguousarray([s["pos"] for s in wl.sources], dtype=np.float64).reshape(-1)
-        teffs = [float(s["Teff"]) for s in wl.sources]
+        teffs = [float(s["Teff"]) for s in wl.sources] + [float(e["Teff"]) for e in ext]
+        self.next = len(ext)
+        self.ext_c = np.ascontiguousarray([e["center"] for e in ext], dtype=np.float64).reshape(-1)
+        self.ext_R = np.ascontiguousarray([e["radius"] for e in ext], dtype=np.float64)
+        # the grid scale L0: outer radius (spherical), largest |wall| of every axis (Cartesian) or
+        # of R and z (cylindrical)
+        axes = {0: (0, 1, 2), 1: (0,), 2: (0, 1)}[self.gtype]
+        self.L0 = max(max(abs(float(self.walls[a][0])), abs(float(self.walls[a][-1]))) for a in axes)
         self.cell_cdf = None
         if wl.cell_source is not None:
             Lc = np.asarray(wl.cell_source["L"], dtype=np.float64).reshape(-1)
@@ -248,6 +257,10 @@ class OracleModel:
         m.img_nx, m.img_ny, m.nimg = self.wl.img_nx, self.wl.img_ny, self.nimg
         m.img_half = float(self.wl.img_half_extent)
         m.img_bin = _ptr(self.img_bin, _ip)
+        m.next = self.next
+        m.ext_c = _ptr(self.ext_c) if self.next else None
+        m.ext_R = _ptr(self.ext_R) if self.next else None
+        m.L0 = self.L0
         self._struct = m
         return m
 

@@ -164,6 +164,8 @@ def cell_volumes(grid_type, walls):
     w1, w2, w3 = (np.asarray(w, dtype=np.float64) for w in walls)
     if grid_type == "cartesian":
         return (np.diff(w3)[:, None, None] * np.diff(w2)[None, :, None] * np.diff(w1)[None, None, :])
+    if grid_type == "cylindrical":       # (R, z, phi): (R_1^2 - R_0^2) / 2 dz dphi
+        return (np.diff(w3)[:, None, None] * np.diff(w2)[None, :, None] * (0.5 * np.diff(w1 ** 2))[None, None, :])
     dr3 = np.diff(w1 ** 3) / 3.0
     dcos = -np.diff(np.cos(w2))
     dph = np.diff(w3)

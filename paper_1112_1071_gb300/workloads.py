@@ -47,8 +47,9 @@ class Workload:
     """A complete problem statement (the input of Sect. 2: density, dust, sources, outputs)."""
 
     name: str
-    grid_type: str                      # "cartesian" or "spherical"
-    walls: list                         # [w1, w2, w3] float64 arrays (cm, or rad for theta/phi)
+    grid_type: str                      # "cartesian", "spherical" or "cylindrical"
+    walls: list                         # [w1, w2, w3] float64 arrays: (x, y, z), (r, theta, phi) or
+                                        # (R, z, phi); cm, rad for the angles
     rho: np.ndarray                     # float32, C-order [n3][n2][n1], g/cm^3
     nu: np.ndarray                      # dust table frequencies, strictly increasing (Hz)
     chi: np.ndarray                     # mass extinction coefficient at nu (cm^2/g)
@@ -57,6 +58,7 @@ class Workload:
     T_nodes: np.ndarray                 # temperature nodes of the emissivity / Planck-mean table (K)
     sources: list = field(default_factory=list)   # dicts: pos (cm, 3), L (erg/s), Teff (K)
     cell_source: dict | None = None     # {"L": float64 [Nc] erg/s, "Teff": K}
+    external_sources: list = field(default_factory=list)  # dicts: center (cm, 3), radius (cm), L, Teff
     obs_incl: np.ndarray = field(default_factory=lambda: np.zeros(0))  # rad
     obs_az: np.ndarray = field(default_factory=lambda: np.zeros(0))    # rad
     nsed: int = 250
@@ -305,6 +307,74 @@ def uniforms(n: int, rng) -> np.ndarray:
     implementations map their Philox words onto."""
     k = rng.integers(0, 1 << 24, n, dtype=np.int64)
     return (k + 1).astype(np.float64) * 2.0 ** -24
+
+
+SIGMA_SB = 5.670374419e-5      # erg cm^-2 s^-1 K^-4
+
+
+def isrf_luminosity(radius_cm: float, dilution: float, T_rad: float) -> float:
+    """Luminosity an external sphere of radius R must emit inwards for an isotropic field of mean
+    intensity J = W B(T_rad) inside it: L = 4 pi R^2 * pi J = 4 pi R^2 W sigma T^4."""
+    return 4.0 * math.pi * radius_cm ** 2 * dilution * SIGMA_SB * T_rad ** 4
+
+
+def isrf_cloud(grid_type: str = "cartesian", n: int = 8, half_extent_au: float = 1e4, tau_550: float = 0.01,
+               dilution: float = 1e-14, T_rad: float = 6000.0, n_packets: int = 200_000, seed: int = 12,
+               r_ext_factor: float = 1.8) -> Workload:
+    """A uniform cloud inside an external isotropic radiation field (Sect. 2.1.1): the external
+    sphere (radius r_ext_factor x the cloud's half extent, centred on it) emits inwards with a
+    diluted blackbody spectrum; no point sources.  grid_type "cartesian" (n^3 box), "spherical"
+    (n shells x n cones x 4 wedges) or "cylindrical" (n x n x 4, |z| <= half extent)."""
+    h = half_extent_au * AU
+    if grid_type == "cartesian":
+        w = np.linspace(-h, h, n + 1)
+        walls = [w, w.copy(), w.copy()]
+        size = 2 * h
+    elif grid_type == "spherical":
+        walls = [np.linspace(0.0, h, n + 1), np.linspace(0.0, math.pi, n + 1), np.linspace(0.0, 2 * math.pi, 5)]
+        size = h
+    else:
+        walls = [np.linspace(0.0, h, n + 1), np.linspace(-h, h, n + 1), np.linspace(0.0, 2 * math.pi, 5)]
+        size = 2 * h
+    shape = tuple(len(x) - 1 for x in walls)
+    rho0 = tau_550 / (chi_at_lambda_um(0.55) * size)
+    rho = np.full(shape[::-1], rho0, dtype=np.float32)
+    nu, chi, alb, g = dust_table()
+    R = r_ext_factor * h * (math.sqrt(3.0) if grid_type == "cartesian" else math.sqrt(2.0))
+    ext = [dict(center=(0.0, 0.0, 0.0), radius=R, L=isrf_luminosity(R, dilution, T_rad), Teff=T_rad)]
+    return Workload(name=f"isrf_{grid_type}", grid_type=grid_type, walls=walls, rho=rho, nu=nu, chi=chi,
+                    albedo=alb, g=g, T_nodes=temperature_nodes(), sources=[], external_sources=ext,
+                    obs_incl=np.radians([30.0]), obs_az=np.zeros(1), n_packets=n_packets, seed=seed)
+
+
+def cylindrical_disk(n_R: int = 120, n_z: int = 96, n_phi: int = 1, r_in_au: float = 1.0,
+                     r_out_au: float = 300.0, tau_550: float = 100.0, h100_au: float = 10.0,
+                     flaring: float = 1.125, n_packets: int = 1_000_000, seed: int = 13,
+                     isrf_dilution: float = 0.0) -> Workload:
+    """The flared disk of Eq. 9's shape on a cylindrical-polar grid (R log-spaced, z uniform over
+    +-4 scale heights at r_out), a 5800 K 1 Lsun star at the centre and, with isrf_dilution > 0,
+    an external isotropic field of a diluted 6000 K blackbody around it (Sect. 2.1.1)."""
+    Rw = r_in_au * AU * (r_out_au / r_in_au) ** (np.arange(n_R + 1) / n_R)
+    zmax = 4 * h100_au * AU * (r_out_au / 100.0) ** flaring
+    zw = np.linspace(-zmax, zmax, n_z + 1)
+    pw = np.linspace(0.0, 2.0 * math.pi, n_phi + 1)
+    Rc = 0.5 * (Rw[1:] + Rw[:-1])
+    zc = 0.5 * (zw[1:] + zw[:-1])
+    ZZ, RR = np.meshgrid(zc, Rc, indexing="ij")
+    hh = h100_au * AU * (RR / (100 * AU)) ** flaring
+    rho0 = tau_550 / (chi_at_lambda_um(0.55) * 100 * AU * math.log(r_out_au / r_in_au))
+    rho2 = rho0 * (RR / (100 * AU)) ** -1.0 * np.exp(-0.5 * (ZZ / hh) ** 2)
+    rho = np.broadcast_to(rho2, (n_phi, n_z, n_R)).astype(np.float32).copy()
+    nu, chi, alb, g = dust_table()
+    ext = []
+    if isrf_dilution > 0:
+        R = 1.01 * math.hypot(r_out_au * AU, zmax)
+        ext = [dict(center=(0.0, 0.0, 0.0), radius=R, L=isrf_luminosity(R, isrf_dilution, 6000.0), Teff=6000.0)]
+    cosi = 0.05 + 0.1 * np.arange(10)
+    return Workload(name="cylindrical_disk", grid_type="cylindrical", walls=[Rw, zw, pw], rho=rho, nu=nu,
+                    chi=chi, albedo=alb, g=g, T_nodes=temperature_nodes(),
+                    sources=[dict(pos=(0.0, 0.0, 0.0), L=LSUN, Teff=5800.0)], external_sources=ext,
+                    obs_incl=np.arccos(cosi), obs_az=np.zeros(10), n_packets=n_packets, seed=seed)
 
 
 WORKLOADS = {

@@ -185,3 +185,85 @@ def test_locate_on_walls_follows_direction():
         u = np.asarray(u, float) / np.linalg.norm(u)
         st = M.lib().or_locate(om._struct, M._ptr(np.zeros(3)), M._ptr(u), M._ptr(out), M._ptr(c, M._ip))
         assert st == 0 and tuple(c) == want
+
+
+def _brute_cyl(walls, p, u):
+    Rw, zw, pw = (np.asarray(w, float) for w in walls)
+    a = u[0] ** 2 + u[1] ** 2
+    b = p[0] * u[0] + p[1] * u[1]
+    c0 = p[0] ** 2 + p[1] ** 2
+    ts = [0.0]
+    t_exit = math.inf
+    if a > 0:
+        for R in Rw:
+            disc = b * b - a * (c0 - R * R)
+            if disc > 0:
+                ts += [t for t in ((-b - math.sqrt(disc)) / a, (-b + math.sqrt(disc)) / a) if t > 0]
+        t_exit = (-b + math.sqrt(b * b - a * (c0 - Rw[-1] ** 2))) / a
+    if u[2] != 0:
+        ts += [float(t) for t in (zw - p[2]) / u[2] if t > 0]
+        t_exit = min(t_exit, ((zw[-1] if u[2] > 0 else zw[0]) - p[2]) / u[2])
+    if len(pw) > 2:
+        for ph in pw[:-1]:
+            nx, ny = -math.sin(ph), math.cos(ph)
+            den = nx * u[0] + ny * u[1]
+            if den != 0:
+                t = -(nx * p[0] + ny * p[1]) / den
+                q = p + t * u
+                if t > 0 and math.cos(ph) * q[0] + math.sin(ph) * q[1] > 0:
+                    ts.append(t)
+    ts = sorted(set(t for t in ts if t <= t_exit) | {t_exit})
+    n = [len(Rw) - 1, len(zw) - 1, len(pw) - 1]
+    segs = []
+    for t0, t1 in zip(ts[:-1], ts[1:]):
+        q = p + 0.5 * (t0 + t1) * u
+        R = math.hypot(q[0], q[1])
+        if R < Rw[0]:
+            continue                      # the inner vacuum cylinder holds no cell
+        ph = math.atan2(q[1], q[0]) % (2 * math.pi)
+        i = int(np.searchsorted(Rw, R, side="right") - 1)
+        j = int(np.searchsorted(zw, q[2], side="right") - 1)
+        k = int(np.searchsorted(pw, ph, side="right") - 1) if n[2] > 1 else 0
+        segs.append(((k * n[1] + j) * n[0] + i, t1 - t0))
+    return segs
+
+
+@pytest.mark.parametrize("hole,nphi", [(True, 4), (False, 1), (True, 1)])
+def test_cylindrical_walk_brute_force(hole, nphi):
+    rng = np.random.default_rng(18 + nphi)
+    Rw = np.array([0.3, 0.5, 0.9, 1.4, 2.0]) if hole else np.array([0.0, 0.5, 0.9, 1.4, 2.0])
+    zw = np.array([-1.5, -0.4, 0.0, 0.3, 1.5])
+    pw = np.array([0.0, 1.0, 2.5, 4.0, 2 * math.pi]) if nphi == 4 else np.array([0.0, 2 * math.pi])
+    walls = [Rw, zw, pw]
+    om = _model("cylindrical", walls)
+    n_done = 0
+    for _ in range(400):
+        while True:
+            p = rng.uniform(-1.99, 1.99, 3)
+            p[2] = rng.uniform(-1.49, 1.49)
+            if math.hypot(p[0], p[1]) < 1.99:
+                break
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        ref = _merge(_brute_cyl(walls, p, u), 1e-9 * 2.0)
+        segc, segl = np.zeros(4096, np.int64), np.zeros(4096)
+        n = M.lib().or_trace(om._struct, M._ptr(p), M._ptr(u), 4096, M._ptr(segc, M._lp), M._ptr(segl))
+        if n < 0:                 # started in the hole and left it through a z plane
+            assert ref == [], (p, u)
+            n_done += 1
+            continue
+        got = _merge(list(zip(segc[:n].tolist(), segl[:n].tolist())), 1e-9 * 2.0)
+        assert [c for c, _ in got] == [c for c, _ in ref], (p, u)
+        np.testing.assert_allclose([l for _, l in got], [l for _, l in ref], rtol=1e-8, atol=1e-9 * 2.0)
+        n_done += 1
+    assert n_done == 400
+
+
+def test_cylindrical_volumes_fill_the_annulus():
+    from oracle import tables as T
+    Rw = np.array([0.3, 0.5, 0.9, 2.0])
+    zw = np.array([-1.0, 0.2, 1.5])
+    pw = np.array([0.0, 1.0, 2 * math.pi])
+    V = T.cell_volumes("cylindrical", [Rw, zw, pw])
+    assert V.shape == (2, 2, 3)
+    assert V.sum() == pytest.approx(math.pi * (2.0 ** 2 - 0.3 ** 2) * 2.5, rel=1e-14)
