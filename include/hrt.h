@@ -73,6 +73,14 @@ int hrt_set_grid_cartesian(hrt_ctx* ctx, int nx, int ny, int nz,
 int hrt_set_grid_spherical(hrt_ctx* ctx, int nr, int nt, int np,
                            const double* rw, const double* tw, const double* pw);
 
+/* Cylindrical-polar grid (Sect. 2.1.2): cylinder radii Rw[0..nR] about the z axis (Rw[0] >= 0;
+ * Rw[0] > 0 leaves an empty inner cylinder that packets cross without interacting), planes
+ * zw[0..nz] (cm), azimuthal walls pw[0..np] with pw[0] = 0, pw[np] = 2 pi and every cell at most
+ * pi wide.  All strictly increasing.  Cells are ordered [phi][z][R].  Not accepted by the batch
+ * (hrt_batch_create); the diffusion approximation stays spherical-polar. */
+int hrt_set_grid_cylindrical(hrt_ctx* ctx, int nR, int nz, int np,
+                             const double* Rw, const double* zw, const double* pw);
+
 /* Dust density per cell (g/cm^3), n = number of cells, finite and >= 0.  Cells of zero density
  * hold no dust: packets cross them without interacting or depositing. */
 int hrt_set_density(hrt_ctx* ctx, const float* rho, int64_t n);
@@ -90,6 +98,14 @@ int hrt_set_dust(hrt_ctx* ctx, int nnu, const double* nu, const double* chi, con
  * luminosity L (erg/s) and a blackbody spectrum of temperature Teff, tabulated on 1000
  * log-spaced frequencies over the dust band and renormalised to carry all of L. */
 int hrt_add_point_source(hrt_ctx* ctx, const double x[3], double L, double Teff);
+
+/* External isotropic source (Sect. 2.1.1: an interstellar radiation field): the sphere of
+ * centre c[3] and radius R (cm) emits L (erg/s) inwards, from points uniform on it, with the
+ * cosine-weighted directions of an isotropic intensity and a blackbody spectrum of temperature
+ * Teff; inside it (and without dust) the mean intensity is J = L / (4 pi^2 R^2).  Packets travel
+ * through vacuum to the grid and enter it (or escape if they miss it); they are not peeled off
+ * at emission (background).  L, R, Teff > 0, c finite; HRT_ESTATE before a grid is set. */
+int hrt_add_external_source(hrt_ctx* ctx, const double c[3], double radius, double L, double Teff);
 
 /* Point source with a user spectrum f_nu on n strictly increasing frequencies (any positive
  * normalisation; the part inside the dust band carries all of L). */

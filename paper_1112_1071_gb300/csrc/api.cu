@@ -74,6 +74,38 @@ int stage_grid(hrt_ctx* ctx) {
         for (int i = 0; i < ctx->n[0]; ++i) va[i] = ctx->w[0][i + 1] - ctx->w[0][i];
         for (int j = 0; j < ctx->n[1]; ++j) vb[j] = ctx->w[1][j + 1] - ctx->w[1][j];
         for (int k = 0; k < ctx->n[2]; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
+    } else if (ctx->gtype == GRID_CYLINDRICAL) {
+        const int nR = ctx->n[0], nz = ctx->n[1], np = ctx->n[2];
+        std::vector<float> rw(nR + 1), r2w(nR + 1), r2wl(nR + 1), zw(nz + 1), phw(np + 1), cph(np + 1), sph(np + 1);
+        std::vector<double> rwd(nR + 1);
+        for (int i = 0; i <= nR; ++i) {
+            rwd[i] = ctx->w[0][i] / ctx->L0;
+            rw[i] = (float)rwd[i];
+            r2w[i] = (float)(rwd[i] * rwd[i]);
+            r2wl[i] = (float)(rwd[i] * rwd[i] - (double)r2w[i]);
+        }
+        for (int j = 0; j <= nz; ++j) zw[j] = (float)(ctx->w[1][j] / ctx->L0);
+        for (int k = 0; k <= np; ++k) {
+            const double p = ctx->w[2][k];
+            phw[k] = (float)p;
+            cph[k] = (float)std::cos(p);
+            sph[k] = (float)std::sin(p);
+        }
+        CK(ctx->d_rw.upload(rw.data(), rw.size(), s), "walls");
+        CK(ctx->d_r2w.upload(r2w.data(), r2w.size(), s), "walls");
+        CK(ctx->d_r2wl.upload(r2wl.data(), r2wl.size(), s), "walls");
+        CK(ctx->d_rwd.upload(rwd.data(), rwd.size(), s), "walls");
+        CK(ctx->d_w2.upload(zw.data(), zw.size(), s), "walls");
+        CK(ctx->d_phw.upload(phw.data(), phw.size(), s), "walls");
+        CK(ctx->d_cph.upload(cph.data(), cph.size(), s), "walls");
+        CK(ctx->d_sph.upload(sph.data(), sph.size(), s), "walls");
+        g.rw = ctx->d_rw.p; g.r2w = ctx->d_r2w.p; g.r2wl = ctx->d_r2wl.p; g.rwd = ctx->d_rwd.p;
+        g.w2 = ctx->d_w2.p;
+        g.phw = ctx->d_phw.p; g.cph = ctx->d_cph.p; g.sph = ctx->d_sph.p;
+        g.r0 = rw[0];
+        for (int i = 0; i < nR; ++i) va[i] = 0.5 * (ctx->w[0][i + 1] * ctx->w[0][i + 1] - ctx->w[0][i] * ctx->w[0][i]);
+        for (int j = 0; j < nz; ++j) vb[j] = ctx->w[1][j + 1] - ctx->w[1][j];
+        for (int k = 0; k < np; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
     } else {
         const int nr = ctx->n[0], nt = ctx->n[1], np = ctx->n[2];
         std::vector<float> rw(nr + 1), r2w(nr + 1), r2wl(nr + 1), thw(nt + 1), cth(nt + 1), sth(nt + 1), phw(np + 1), cph(np + 1),
@@ -202,8 +234,9 @@ int stage_dust(hrt_ctx* ctx) {
 int stage_sources(hrt_ctx* ctx) {
     const cudaStream_t s = ctx->stream;
     const int npt = (int)ctx->pts.size();
+    const int next = (int)ctx->ext.size();
     const bool cell = !ctx->Lcell.empty();
-    const int nsrc = npt + (cell ? 1 : 0);
+    const int nsrc = npt + next + (cell ? 1 : 0);
     std::vector<double> L(nsrc), teff(nsrc), unu, uf;
     std::vector<int> uoff(nsrc, 0), un(nsrc, 0);
     std::vector<float> pos(3 * std::max(npt, 1), 0.f);
@@ -216,6 +249,17 @@ int stage_sources(hrt_ctx* ctx) {
         unu.insert(unu.end(), ctx->pts[i].unu.begin(), ctx->pts[i].unu.end());
         uf.insert(uf.end(), ctx->pts[i].uf.begin(), ctx->pts[i].uf.end());
     }
+    std::vector<float> ec(3 * std::max(next, 1), 0.f), eR(std::max(next, 1), 0.f);
+    for (int e = 0; e < next; ++e) {
+        L[npt + e] = ctx->ext[e].L;
+        teff[npt + e] = ctx->ext[e].teff;
+        uoff[npt + e] = (int)unu.size();
+        un[npt + e] = 0;
+        for (int a = 0; a < 3; ++a) ec[3 * e + a] = (float)(ctx->ext[e].c[a] / ctx->L0);
+        eR[e] = (float)(ctx->ext[e].R / ctx->L0);
+    }
+    CK(ctx->d_ext_c.upload(ec.data(), ec.size(), s), "external sources");
+    CK(ctx->d_ext_R.upload(eR.data(), eR.size(), s), "external sources");
     if (cell) {
         double tot = 0.0;
         std::vector<double> cc(ctx->Lcell.size());
@@ -223,8 +267,8 @@ int stage_sources(hrt_ctx* ctx) {
         for (auto& v : cc) v /= tot;
         cc.back() = 1.0;
         CK(ctx->d_cell_cdf.upload(cc.data(), cc.size(), s), "cell source");
-        L[npt] = tot;
-        teff[npt] = ctx->cell_teff;
+        L[npt + next] = tot;
+        teff[npt + next] = ctx->cell_teff;
     }
     double cum = 0.0;
     std::vector<double> cdf(nsrc);
@@ -258,6 +302,9 @@ int stage_sources(hrt_ctx* ctx) {
     S.pos = ctx->d_src_pos.p; S.cdf = ctx->d_src_cdf.p; S.spec_nu = ctx->d_spec_nu.p; S.spec_cdf = ctx->d_spec_cdf.p;
     S.cell_cdf = cell ? ctx->d_cell_cdf.p : nullptr;
     S.col = nullptr;            // set per imaging pass
+    S.next = next;
+    S.ext_c = ctx->d_ext_c.p;
+    S.ext_R = ctx->d_ext_R.p;
     ctx->dirty_src = false;
     return HRT_OK;
 }
@@ -308,7 +355,7 @@ int prepare(hrt_ctx* ctx) {
     if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "grid not set");
     if ((int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "density not set");
     if (ctx->nu.empty()) return ctx->fail(HRT_ESTATE, "dust not set");
-    if (ctx->pts.empty() && ctx->Lcell.empty()) return ctx->fail(HRT_ESTATE, "no sources");
+    if (ctx->pts.empty() && ctx->ext.empty() && ctx->Lcell.empty()) return ctx->fail(HRT_ESTATE, "no sources");
     int rc;
     if (ctx->dirty_grid && (rc = stage_grid(ctx)) != HRT_OK) return rc;
     if (ctx->dirty_dust && (rc = stage_dust(ctx)) != HRT_OK) return rc;
@@ -365,7 +412,7 @@ int hrt_destroy(hrt_ctx* ctx) {
                     &ctx->d_thw, &ctx->d_cth, &ctx->d_sth, &ctx->d_phw, &ctx->d_cph, &ctx->d_sph, &ctx->d_lnu,
                     &ctx->d_inv_dlnu, &ctx->d_lchi, &ctx->d_alb, &ctx->d_nuf, &ctx->d_cdf_emit, &ctx->d_src_pos,
                     &ctx->d_spec_nu, &ctx->d_spec_cdf, &ctx->d_obs_n, &ctx->d_obs_ex, &ctx->d_obs_ey,
-                    &ctx->d_src_col})
+                    &ctx->d_src_col, &ctx->d_ext_c, &ctx->d_ext_R})
         b->release();
     for (auto* b : {&ctx->d_rwd, &ctx->d_cthd, &ctx->d_sthd, &ctx->d_va, &ctx->d_vb, &ctx->d_vc, &ctx->d_nu,
                     &ctx->d_kappa, &ctx->d_Tn, &ctx->d_lnT, &ctx->d_E, &ctx->d_lnE, &ctx->d_src_cdf, &ctx->d_cell_cdf,
@@ -409,6 +456,13 @@ static int set_grid(hrt_ctx* ctx, int type, int n1, int n2, int n3, const double
     for (int a = 0; a < 3; ++a)
         if (!finite_all(w[a], n[a] + 1) || !increasing(w[a], n[a] + 1))
             return ctx->fail(HRT_EINVAL, "grid: walls of axis %d not finite and strictly increasing", a);
+    if (type == GRID_CYLINDRICAL) {
+        if (w1[0] < 0) return ctx->fail(HRT_EINVAL, "grid: negative cylinder radius");
+        if (w3[0] != 0.0 || std::fabs(w3[n3] - 2 * PI) > 1e-12) return ctx->fail(HRT_EINVAL, "grid: phi walls must span [0, 2 pi]");
+        if (n3 > 1)
+            for (int k = 0; k < n3; ++k)
+                if (w3[k + 1] - w3[k] > PI + 1e-12) return ctx->fail(HRT_EINVAL, "grid: phi cells wider than pi");
+    }
     if (type == GRID_SPHERICAL) {
         if (w1[0] < 0) return ctx->fail(HRT_EINVAL, "grid: negative radius");
         if (w2[0] != 0.0 || std::fabs(w2[n2] - PI) > 1e-12) return ctx->fail(HRT_EINVAL, "grid: theta walls must span [0, pi]");
@@ -422,13 +476,14 @@ static int set_grid(hrt_ctx* ctx, int type, int n1, int n2, int n3, const double
     for (int a = 0; a < 3; ++a) {
         ctx->n[a] = n[a];
         ctx->w[a].assign(w[a], w[a] + n[a] + 1);
-        if (type == GRID_CARTESIAN || a == 0)
+        if (type == GRID_CARTESIAN || a == 0 || (type == GRID_CYLINDRICAL && a == 1))
             L0 = std::max(L0, std::max(std::fabs(w[a][0]), std::fabs(w[a][n[a]])));
     }
     if (type == GRID_SPHERICAL) {
         ctx->w[1].back() = PI;
         ctx->w[2].back() = 2 * PI;
     }
+    if (type == GRID_CYLINDRICAL) ctx->w[2].back() = 2 * PI;
     ctx->L0 = L0 > 0 ? L0 : 1.0;
     ctx->rho.clear();
     ctx->Lcell.clear();
@@ -444,6 +499,10 @@ int hrt_set_grid_cartesian(hrt_ctx* ctx, int nx, int ny, int nz, const double* x
 
 int hrt_set_grid_spherical(hrt_ctx* ctx, int nr, int nt, int np, const double* rw, const double* tw, const double* pw) {
     return set_grid(ctx, GRID_SPHERICAL, nr, nt, np, rw, tw, pw);
+}
+
+int hrt_set_grid_cylindrical(hrt_ctx* ctx, int nR, int nz, int np, const double* Rw, const double* zw, const double* pw) {
+    return set_grid(ctx, GRID_CYLINDRICAL, nR, nz, np, Rw, zw, pw);
 }
 
 int hrt_set_density(hrt_ctx* ctx, const float* rho, int64_t n) {
@@ -536,9 +595,28 @@ int hrt_set_cell_source(hrt_ctx* ctx, const double* Lcell, int64_t n, double Tef
     return HRT_OK;
 }
 
+int hrt_add_external_source(hrt_ctx* ctx, const double c[3], double radius, double L, double Teff) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "external source before grid");
+    if (!c || !std::isfinite(c[0]) || !std::isfinite(c[1]) || !std::isfinite(c[2]))
+        return ctx->fail(HRT_EINVAL, "external source: centre not finite");
+    if (!(radius > 0) || !std::isfinite(radius)) return ctx->fail(HRT_EINVAL, "external source: radius must be > 0");
+    if (!(L > 0) || !std::isfinite(L)) return ctx->fail(HRT_EINVAL, "external source: L must be > 0");
+    if (!(Teff > 0) || !std::isfinite(Teff)) return ctx->fail(HRT_EINVAL, "external source: Teff must be > 0");
+    ExtSrc e;
+    for (int a = 0; a < 3; ++a) e.c[a] = c[a];
+    e.R = radius;
+    e.L = L;
+    e.teff = Teff;
+    ctx->ext.push_back(e);
+    ctx->dirty_src = true;
+    return HRT_OK;
+}
+
 int hrt_clear_sources(hrt_ctx* ctx) {
     if (!ctx) return HRT_EINVAL;
     ctx->pts.clear();
+    ctx->ext.clear();
     ctx->Lcell.clear();
     ctx->dirty_src = true;
     return HRT_OK;

@@ -274,7 +274,8 @@ int hrt_batch_create(hrt_batch** out, hrt_ctx* const* models, int n) {
     if (!out || !models || n < 1) return HRT_EINVAL;
     *out = nullptr;
     for (int m = 0; m < n; ++m)
-        if (!models[m] || models[m]->device != models[0]->device) return HRT_EINVAL;
+        if (!models[m] || models[m]->device != models[0]->device || models[m]->gtype == GRID_CYLINDRICAL)
+            return HRT_EINVAL;          // the batch runs Cartesian and spherical-polar models
     hrt_batch* b = new hrt_batch();
     b->models.assign(models, models + n);
     b->device = models[0]->device;

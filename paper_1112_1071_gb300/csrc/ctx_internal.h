@@ -51,6 +51,14 @@ struct PointSrc {
     std::vector<double> unu, uf;
 };
 
+// External isotropic source (Sect. 2.1.1): a sphere emitting inwards.
+struct ExtSrc {
+    double c[3];
+    double R;
+    double L;
+    double teff;
+};
+
 }  // namespace hrt
 
 using hrt::DBuf;
@@ -60,6 +68,7 @@ using hrt::DevGrid;
 using hrt::DevObs;
 using hrt::DevSources;
 using hrt::PointSrc;
+using hrt::ExtSrc;
 
 struct hrt_ctx {
     int device = 0;
@@ -79,6 +88,7 @@ struct hrt_ctx {
     std::vector<double> nu, chi, alb, Tn;
     double g = 0.0;
     std::vector<PointSrc> pts;
+    std::vector<hrt::ExtSrc> ext;
     std::vector<double> Lcell;
     double cell_teff = 0.0;
     int nobs = 0, nsed = DEFAULT_NSED, img_nx = 0, img_ny = 0, nimg = 0;
@@ -94,7 +104,7 @@ struct hrt_ctx {
     DBuf<float> d_src_pos, d_spec_nu, d_spec_cdf;
     DBuf<double> d_src_cdf, d_cell_cdf, d_spec_nud, d_teff, d_unu, d_uf;
     DBuf<int> d_uoff, d_un;
-    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey, d_src_col;
+    DBuf<float> d_obs_n, d_obs_ex, d_obs_ey, d_src_col, d_ext_c, d_ext_R;
     DBuf<int32_t> d_img_bin;
     // ---- device state
     DBuf<double> d_T, d_adot, d_acc, d_sed, d_img;

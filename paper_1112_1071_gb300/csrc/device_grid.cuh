@@ -424,6 +424,149 @@ __device__ __forceinline__ bool sph_locate(const DevGrid& g, Ray& r) {
     return true;
 }
 
+// ================================================================ cylindrical-polar (R, z, phi)
+// Walls: cylinders R_i about the z axis, planes z_j (the w2 table) and half-planes phi_k; an
+// inner vacuum cylinder when R_0 > 0.  A cylinder's quadratic a s^2 + 2 b s + c = 0 has
+// a = u_x^2 + u_y^2, b = p_R . u_R and c = |p_R|^2 - R_w^2; c is formed with the rounding errors
+// carried as for spheres, and a ray grazing the inner cylinder redoes its discriminant in FP64.
+
+__device__ __forceinline__ float cyl_c(float px, float py, float w_hi, float w_lo) {
+    const float x2 = __fmul_rn(px, px), y2 = __fmul_rn(py, py);
+    const float ex = fmaf(px, px, -x2), ey = fmaf(py, py, -y2);
+    float s1, e1, s2, e2;
+    two_sum(x2, y2, s1, e1);
+    two_sum(s1, -w_hi, s2, e2);
+    return __fadd_rn(s2, __fadd_rn(__fadd_rn(e1, e2), __fsub_rn(__fadd_rn(ex, ey), w_lo)));
+}
+
+__device__ __forceinline__ float cyl_exit(const DevGrid& g, const Ray& r, int& axis, int& dir) {
+    const float a = r.u.x * r.u.x + r.u.y * r.u.y;
+    const float b = r.p.x * r.u.x + r.p.y * r.u.y;
+    const float R2 = r.p.x * r.p.x + r.p.y * r.p.y;
+    const float tol = 2e-6f * sqrtf(R2 + r.p.z * r.p.z) + 1e-30f;
+    float best = F_INF;
+    axis = -1;
+    dir = 0;
+    if (a > 0.f) {
+        // outer cylinder: the far root, always ahead of a point inside
+        const float co = cyl_c(r.p.x, r.p.y, __ldg(g.r2w + r.i + 1), __ldg(g.r2wl + r.i + 1));
+        const float sq = sqrtf(fmaxf(fmaf(b, b, -a * co), 0.f));
+        const float s = b > 0.f ? -co / (b + sq) : (-b + sq) / a;
+        best = fmaxf(s, 0.f);
+        axis = 0;
+        dir = 1;
+        // inner cylinder, entered only while clearly moving inwards (as for the inner sphere)
+        if (b < -1e-6f * sqrtf(R2 * a) && __ldg(g.rw + r.i) > 0.f) {
+            const float ci = cyl_c(r.p.x, r.p.y, __ldg(g.r2w + r.i), __ldg(g.r2wl + r.i));
+            float disc = fmaf(b, b, -a * ci);
+            float bb = b;
+            if (fabsf(disc) < 0x1p-10f * b * b) {           // grazing the inner cylinder
+                const double px = r.p.x, py = r.p.y, ux = r.u.x, uy = r.u.y;
+                const double ad = fma(ux, ux, uy * uy), bd = fma(px, ux, py * uy);
+                const double ri = __ldg(g.rwd + r.i);
+                const double cd = fma(px, px, fma(py, py, -ri * ri));
+                disc = (float)fma(bd, bd, -ad * cd);
+                bb = (float)bd;
+            }
+            if (disc >= 0.f) {
+                const float si = fmaxf(ci / (-bb + sqrtf(disc)), 0.f);
+                if (si < best) { best = si; dir = -1; }
+            }
+        }
+    }
+    if (r.u.z != 0.f) {
+        const float zw = r.u.z > 0.f ? __ldg(g.w2 + r.j + 1) : __ldg(g.w2 + r.j);
+        const float s = fmaxf((zw - r.p.z) * r.inv.z, 0.f);
+        if (s < best) { best = s; axis = 1; dir = r.u.z > 0.f ? 1 : -1; }
+    }
+    if (g.n3 > 1) {
+        float s = phi_root(r, __ldg(g.cph + r.k), __ldg(g.sph + r.k), -1, tol);
+        if (s < best) { best = s; axis = 2; dir = -1; }
+        s = phi_root(r, __ldg(g.cph + r.k + 1), __ldg(g.sph + r.k + 1), +1, tol);
+        if (s < best) { best = s; axis = 2; dir = 1; }
+    }
+    return best;
+}
+
+// Azimuthal cell of a point (direction breaks ties on walls; on the axis, the direction's phi).
+__device__ __forceinline__ int phi_cell(const DevGrid& g, const Ray& r) {
+    if (g.n3 <= 1) return 0;
+    float ph, vp;
+    if (r.p.x * r.p.x + r.p.y * r.p.y == 0.f) { ph = wrap_2pi(atan2f(r.u.y, r.u.x)); vp = 0.f; }
+    else { ph = wrap_2pi(atan2f(r.p.y, r.p.x)); vp = r.p.x * r.u.y - r.p.y * r.u.x; }
+    if (ph == 0.f && !(vp > 0.f)) return g.n3 - 1;
+    const int k = locate_axis(g.phw, g.n3, ph, vp);
+    return k < 0 ? g.n3 - 1 : k;
+}
+
+// Cross the inner vacuum cylinder to its far side (FP64); true when the ray leaves the grid on
+// the way (through a z plane, or running along the axis).
+__device__ __forceinline__ bool cyl_cross_hole(const DevGrid& g, Ray& r) {
+    const double px = r.p.x, py = r.p.y, ux = r.u.x, uy = r.u.y;
+    const double a = fma(ux, ux, uy * uy);
+    if (!(a > 0.0)) return true;
+    const double R0 = __ldg(g.rwd);
+    const double b = fma(px, ux, py * uy);
+    const double c = fma(px, px, fma(py, py, -R0 * R0));
+    const double sq = sqrt(fmax(fma(b, b, -a * c), 0.0));
+    double s = b > 0.0 ? -c / (b + sq) : (-b + sq) / a;
+    if (s < 0.0) s = 0.0;
+    r.p = make_float3((float)(px + s * ux), (float)(py + s * uy), (float)((double)r.p.z + s * (double)r.u.z));
+    const int j = locate_axis(g.w2, g.n2, r.p.z, r.u.z);
+    if (j < 0) return true;
+    r.i = 0;
+    r.j = j;
+    r.k = phi_cell(g, r);
+    r.ci = lin(g, r.i, r.j, r.k);
+    return false;
+}
+
+__device__ __forceinline__ bool cyl_step(const DevGrid& g, Ray& r, float l, int axis, int dir) {
+    r.p.x += l * r.u.x;
+    r.p.y += l * r.u.y;
+    r.p.z += l * r.u.z;
+    if (axis == 0) {
+        r.i += dir;
+        if (r.i >= g.n1) return true;
+        if (r.i < 0) return cyl_cross_hole(g, r);
+        // put the point back on the cylinder it crossed
+        const float Rw = __ldg(g.rw + r.i + (dir < 0 ? 1 : 0));
+        const float sc = Rw * rsqrtf(r.p.x * r.p.x + r.p.y * r.p.y);
+        r.p.x *= sc;
+        r.p.y *= sc;
+        r.ci += dir;
+        return false;
+    }
+    if (axis == 1) {
+        r.j += dir;
+        if (r.j < 0 || r.j >= g.n2) return true;
+        r.p.z = __ldg(g.w2 + r.j + (dir < 0 ? 1 : 0));
+        r.ci += dir * g.n1;
+        return false;
+    }
+    r.k += dir;
+    if (r.k < 0) r.k += g.n3;
+    if (r.k >= g.n3) r.k -= g.n3;
+    r.ci = lin(g, r.i, r.j, r.k);
+    return false;
+}
+
+__device__ __forceinline__ bool cyl_locate(const DevGrid& g, Ray& r) {
+    const int j = locate_axis(g.w2, g.n2, r.p.z, r.u.z);
+    if (j < 0) return false;
+    const float R = sqrtf(r.p.x * r.p.x + r.p.y * r.p.y);
+    const float vR = r.p.x * r.u.x + r.p.y * r.u.y;
+    const float R0 = __ldg(g.rw);
+    if (R0 > 0.f && (R < R0 || (R == R0 && !(vR > 0.f)))) return !cyl_cross_hole(g, r);
+    const int i = locate_axis(g.rw, g.n1, R, vR);
+    if (i < 0) return false;
+    r.i = i;
+    r.j = j;
+    r.k = phi_cell(g, r);
+    r.ci = lin(g, r.i, r.j, r.k);
+    return true;
+}
+
 // ================================================================ dispatch
 template <int G>
 __device__ __forceinline__ float cell_exit(const DevGrid& g, const Ray& r, int& axis, int& dir) {
@@ -431,21 +574,111 @@ __device__ __forceinline__ float cell_exit(const DevGrid& g, const Ray& r, int& 
         const float l = cart_exit(g, r, axis);
         dir = 0;
         return l;
-    } else {
+    } else if constexpr (G == GRID_SPHERICAL) {
         return sph_exit(g, r, axis, dir);
+    } else {
+        return cyl_exit(g, r, axis, dir);
     }
 }
 
 template <int G>
 __device__ __forceinline__ bool cell_step(const DevGrid& g, Ray& r, float l, int axis, int dir) {
     if constexpr (G == GRID_CARTESIAN) return cart_step(g, r, l, axis);
-    else return sph_step(g, r, l, axis, dir);
+    else if constexpr (G == GRID_SPHERICAL) return sph_step(g, r, l, axis, dir);
+    else return cyl_step(g, r, l, axis, dir);
 }
 
 template <int G>
 __device__ __forceinline__ bool grid_locate(const DevGrid& g, Ray& r) {
     if constexpr (G == GRID_CARTESIAN) return cart_locate(g, r);
-    else return sph_locate(g, r);
+    else if constexpr (G == GRID_SPHERICAL) return sph_locate(g, r);
+    else return cyl_locate(g, r);
+}
+
+// ================================================================ grid entry from outside
+// Cell index of v clamped into [w_0, w_n] (no direction rule: used only at the outer boundary).
+__device__ __forceinline__ int clamp_axis(const float* __restrict__ w, int n, float v) {
+    if (!(v > __ldg(w))) return 0;
+    if (!(v < __ldg(w + n))) return n - 1;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(w + mid) <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Locate a packet that has just crossed the grid's outer boundary inwards (grid_entry, then a
+// step of 1e-6 along the ray).  On a ray that enters at a glancing angle that step is a radial
+// depth below FP32 rounding of the position, which can leave the point just outside; such a
+// point belongs to the boundary cell it is entering, so the outer index is clamped there.
+template <int G>
+__device__ __forceinline__ bool grid_locate_entry(const DevGrid& g, Ray& r) {
+    if (grid_locate<G>(g, r)) return true;
+    if constexpr (G == GRID_CARTESIAN) {
+        r.i = clamp_axis(g.w1, g.n1, r.p.x);
+        r.j = clamp_axis(g.w2, g.n2, r.p.y);
+        r.k = clamp_axis(g.w3, g.n3, r.p.z);
+    } else if constexpr (G == GRID_SPHERICAL) {
+        r.i = clamp_axis(g.rw, g.n1, sqrtf(dot3(r.p, r.p)));
+        sph_angles(g, r);
+    } else {
+        const float R = sqrtf(r.p.x * r.p.x + r.p.y * r.p.y);
+        if (R < __ldg(g.rw)) return false;                  // the inner cylinder is not the boundary
+        r.i = clamp_axis(g.rw, g.n1, R);
+        r.j = clamp_axis(g.w2, g.n2, r.p.z);
+        r.k = phi_cell(g, r);
+    }
+    r.ci = lin(g, r.i, r.j, r.k);
+    return true;
+}
+
+// Parameter t >= 0 at which p + t u first enters the grid's outer boundary (0 when p is inside),
+// or -1 when the ray misses the grid (FP32, scaled lengths).
+template <int G>
+__device__ __forceinline__ float grid_entry(const DevGrid& g, float3 p, float3 u) {
+    float tmin = -F_INF, tmax = F_INF;
+    if constexpr (G == GRID_SPHERICAL) {
+        const float ro = __ldg(g.rw + g.n1);
+        const float b = dot3(p, u), c = fmaf(-ro, ro, dot3(p, p));
+        if (c <= 0.f) return 0.f;
+        const float disc = b * b - c;
+        if (disc < 0.f || b >= 0.f) return -1.f;
+        return c / (-b + sqrtf(disc));
+    } else {
+        const float* ws[3] = {g.w1, g.w2, g.w3};
+        const int ns[3] = {g.n1, g.n2, g.n3};
+        const float pc[3] = {p.x, p.y, p.z}, uc[3] = {u.x, u.y, u.z};
+        if constexpr (G == GRID_CYLINDRICAL) {
+            const float ro = __ldg(g.rw + g.n1);
+            const float a = u.x * u.x + u.y * u.y, b = p.x * u.x + p.y * u.y;
+            const float c = fmaf(-ro, ro, p.x * p.x + p.y * p.y);
+            if (a == 0.f) {
+                if (c > 0.f) return -1.f;
+            } else {
+                const float disc = b * b - a * c;
+                if (disc < 0.f) return -1.f;
+                const float sq = sqrtf(disc);
+                tmin = (-b - sq) / a;
+                tmax = (-b + sq) / a;
+            }
+        }
+        for (int ax = (G == GRID_CYLINDRICAL ? 2 : 0); ax < 3; ++ax) {
+            // Cartesian: x, y, z; cylindrical: only z (the w2 walls)
+            const int wa = G == GRID_CYLINDRICAL ? 1 : ax;
+            const float* w = ws[wa];
+            const float lo = __ldg(w), hi = __ldg(w + ns[wa]);
+            if (uc[ax] == 0.f) {
+                if (pc[ax] < lo || pc[ax] > hi) return -1.f;
+                continue;
+            }
+            const float t1 = (lo - pc[ax]) / uc[ax], t2 = (hi - pc[ax]) / uc[ax];
+            tmin = fmaxf(tmin, fminf(t1, t2));
+            tmax = fminf(tmax, fmaxf(t1, t2));
+        }
+    }
+    if (tmax < fmaxf(tmin, 0.f)) return -1.f;
+    return fmaxf(tmin, 0.f);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -483,7 +716,7 @@ __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi,
         ++ncross;
         if (tau > tau_stop) return tau;
         if (cell_step<G>(g, r, l, axis, dir)) return tau;
-        if constexpr (G == GRID_SPHERICAL) {
+        if constexpr (G != GRID_CARTESIAN) {
             if (!tiny_step(r, l)) zero_run = 0;
             else if (++zero_run > ZERO_RUN_LIMIT) { nudge(r); zero_run = 0; }
         }

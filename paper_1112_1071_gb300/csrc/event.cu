@@ -239,6 +239,8 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 } else if (!emit_packet<G>(g, d, s, o, a, t, st.sed, (int64_t)q, pk, lc, false)) {
                     lc.v[C_ESCAPED]++;
                     lc.v[C_PACKETS_DONE]++;
+                } else if (pk.src >= s.npoint && pk.src < s.npoint + s.next) {
+                    start_walk();               // external field: background, not peeled off
                 } else {
                     porg = pk.last_origin;
                     after_event(PEEL_ISO, pk.emit_relocate, pk.src < s.npoint);
@@ -299,7 +301,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 }
                 if (!stop) {
                     if (cell_step<G>(g, pk.r, l, axis, dir)) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
-                    if constexpr (G == GRID_SPHERICAL) {
+                    if constexpr (G != GRID_CARTESIAN) {
                         if (!tiny_step(pk.r, l)) zero_run = 0;
                         else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
                     }
@@ -366,7 +368,7 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     // the walk phase while at least 20 (spherical Lucy iteration) or 24 (imaging pass; Cartesian
     // runs of >= 4M packets) lanes walk, 12 for small Cartesian runs whose tail dominates
     int rg_default = DEFAULT_REGROUP;
-    if (job.grid.type == GRID_SPHERICAL) rg_default = peel ? 24 : 20;
+    if (job.grid.type != GRID_CARTESIAN) rg_default = peel ? 24 : 20;
     else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 24;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
@@ -374,6 +376,9 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     if (job.grid.type == GRID_CARTESIAN)
         return peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
                     : launch_event_shape<GRID_CARTESIAN, false>(j, ll, bps, s);
+    if (job.grid.type == GRID_CYLINDRICAL)
+        return peel ? launch_event_shape<GRID_CYLINDRICAL, true>(j, ll, bps, s)
+                    : launch_event_shape<GRID_CYLINDRICAL, false>(j, ll, bps, s);
     return peel ? launch_event_shape<GRID_SPHERICAL, true>(j, ll, bps, s)
                 : launch_event_shape<GRID_SPHERICAL, false>(j, ll, bps, s);
 }

@@ -6,18 +6,19 @@
 
 namespace hrt {
 
-enum GridType : int32_t { GRID_CARTESIAN = 0, GRID_SPHERICAL = 1 };
+enum GridType : int32_t { GRID_CARTESIAN = 0, GRID_SPHERICAL = 1, GRID_CYLINDRICAL = 2 };
 
 struct DevGrid {
     int32_t type;
-    int32_t n1, n2, n3;            // cells per axis (x,y,z) or (r,theta,phi)
+    int32_t n1, n2, n3;            // cells per axis (x,y,z), (r,theta,phi) or (R,z,phi)
     int64_t ncells;
     const float* rhoL;             // [ncells] rho * L0 (so dtau = rhoL * chi * l)
-    // Cartesian walls (scaled)
+    // Cartesian walls (scaled); cylindrical: w2 holds the z walls
     const float* w1;
     const float* w2;
     const float* w3;
-    // spherical: radii (scaled) and squares, polar walls (angle, cos, sin), azimuthal walls
+    // spherical: radii (scaled) and squares, polar walls (angle, cos, sin), azimuthal walls;
+    // cylindrical: the cylinder radii R in rw/r2w/r2wl/rwd and the azimuthal walls
     const float* rw;               // [n1+1]
     const float* r2w;              // [n1+1] r^2 rounded to FP32
     const float* r2wl;             // [n1+1] r^2 - r2w (the FP32 pair holds r^2 to ~2^-48)
@@ -60,6 +61,10 @@ struct DevSources {
     const float* spec_nu;          // [nspec]
     const float* spec_cdf;         // [nsrc][nspec]
     const double* cell_cdf;        // [ncells] cumulative cell luminosity or null
+    int32_t next;                  // external isotropic sources: indices npoint .. npoint+next-1
+    int32_t pad_ext;
+    const float* ext_c;            // [next][3] sphere centres (scaled)
+    const float* ext_R;            // [next] sphere radii (scaled)
     const float* col;              // [npoint][nobs] sum of rhoL l from each point source along each
                                    // observer direction (imaging passes), or null
 };

@@ -109,7 +109,8 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
 }
 
 // Cell c and a point uniform in its volume from three uniforms (Cartesian: each coordinate;
-// spherical: r^3, cos(theta) and phi uniform), as for emission from a cell.
+// spherical: r^3, cos(theta) and phi uniform; cylindrical: R^2, z and phi uniform), as for
+// emission from a cell.
 template <int G>
 __device__ __forceinline__ void place_in_cell(const DevGrid& g, int64_t c, float f0, float f1, float f2, Ray& r) {
     r.i = (int)(c % g.n1);
@@ -120,6 +121,15 @@ __device__ __forceinline__ void place_in_cell(const DevGrid& g, int64_t c, float
         const float x0 = __ldg(g.w1 + r.i), y0 = __ldg(g.w2 + r.j), z0 = __ldg(g.w3 + r.k);
         r.p = make_float3(x0 + f0 * (__ldg(g.w1 + r.i + 1) - x0), y0 + f1 * (__ldg(g.w2 + r.j + 1) - y0),
                           z0 + f2 * (__ldg(g.w3 + r.k + 1) - z0));
+    } else if constexpr (G == GRID_CYLINDRICAL) {     // R^2, z, phi uniform
+        const double R0 = __ldg(g.rwd + r.i), R1 = __ldg(g.rwd + r.i + 1);
+        const float R = (float)sqrt(R0 * R0 + (double)f0 * (R1 * R1 - R0 * R0));
+        const float z0 = __ldg(g.w2 + r.j);
+        const float ph0 = __ldg(g.phw + r.k);
+        const float ph = ph0 + f2 * (__ldg(g.phw + r.k + 1) - ph0);
+        float sp, cp;
+        sincosf(ph, &sp, &cp);
+        r.p = make_float3(R * cp, R * sp, z0 + f1 * (__ldg(g.w2 + r.j + 1) - z0));
     } else {
         const double r0 = __ldg(g.rwd + r.i), r1 = __ldg(g.rwd + r.i + 1);
         const double rad = cbrt(r0 * r0 * r0 + (double)f0 * (r1 * r1 * r1 - r0 * r0 * r0));
@@ -157,6 +167,38 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
         if (a.peel && !a.rt && inline_peel)     // raytraced instead when a.rt (Sect. 2.6.3)
             peel_event<G>(g, d, o, a, t, sed_s, at, pk.r.u, PEEL_ISO, true, pk.dust.chi, pk.sbin, lc,
                           s.col ? s.col + (int64_t)src * o.nobs : nullptr);
+    } else if (src < s.npoint + s.next) {
+        // external isotropic source (Sect. 2.1.1): a point uniform on its sphere, a direction into
+        // it with the cosine-weighted distribution of an isotropic intensity (cos = sqrt(u) about
+        // the inward normal, azimuth in the normal's fixed frame); the packet travels through
+        // vacuum to the grid and enters it 1e-6 L0 deep, or escapes; no peel-off (background)
+        const int e = src - s.npoint;
+        const float u1 = pk.rng.next(), u2 = pk.rng.next();
+        const float3 nh = isotropic_dir(u1, u2);
+        const float R = __ldg(s.ext_R + e);
+        const float3 p = make_float3(__ldg(s.ext_c + 3 * e) + R * nh.x, __ldg(s.ext_c + 3 * e + 1) + R * nh.y,
+                                     __ldg(s.ext_c + 3 * e + 2) + R * nh.z);
+        const float u3 = pk.rng.next(), u4 = pk.rng.next();
+        float3 e1 = fabsf(nh.z) < 0.99999f ? make_float3(-nh.y, nh.x, 0.f) : make_float3(nh.z, 0.f, -nh.x);
+        const float ie = rsqrtf(e1.x * e1.x + e1.y * e1.y + e1.z * e1.z);
+        e1.x *= ie; e1.y *= ie; e1.z *= ie;
+        const float3 e2 = make_float3(nh.y * e1.z - nh.z * e1.y, nh.z * e1.x - nh.x * e1.z, nh.x * e1.y - nh.y * e1.x);
+        const float ct = sqrtf(u3), st = sqrtf(1.f - u3);
+        float sp, cp;
+        sincospif(2.f * u4, &sp, &cp);
+        float3 u = make_float3(-ct * nh.x + st * (cp * e1.x + sp * e2.x), -ct * nh.y + st * (cp * e1.y + sp * e2.y),
+                               -ct * nh.z + st * (cp * e1.z + sp * e2.z));
+        const float iu = rsqrtf(u.x * u.x + u.y * u.y + u.z * u.z);
+        u.x *= iu; u.y *= iu; u.z *= iu;
+        set_frequency(pk, d, o, sample_table(s.spec_nu, s.spec_cdf + (int64_t)src * s.nspec, s.nspec, pk.rng.next()));
+        pk.emit_relocate = 0;
+        const float t = grid_entry<G>(g, p, u);
+        if (t < 0.f) return false;
+        const float te = t + 1e-6f;
+        pk.r.p = make_float3(p.x + te * u.x, p.y + te * u.y, p.z + te * u.z);
+        set_dir(pk.r, u);
+        pk.last_origin = pk.r.p;
+        if (!grid_locate_entry<G>(g, pk.r)) return false;
     } else {
         pk.emit_relocate = 0;
         const int64_t c = select_cdf<double>(s.cell_cdf, g.ncells, (double)pk.rng.next());

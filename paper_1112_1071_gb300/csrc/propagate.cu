@@ -25,7 +25,7 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
     for (;;) {
         int axis, dir;
         const float l = cell_exit<G>(g, pk.r, axis, dir);
-        if constexpr (G == GRID_SPHERICAL) {
+        if constexpr (G != GRID_CARTESIAN) {
             if (!tiny_step(pk.r, l)) zero_run = 0;
             else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
         }
@@ -125,6 +125,7 @@ cudaError_t launch_source_columns(const DevGrid& g, const DevSources& src, const
     if (n <= 0) return cudaSuccess;
     const int blocks = (n + 127) / 128;
     if (g.type == GRID_CARTESIAN) k_source_columns<GRID_CARTESIAN><<<blocks, 128, 0, s>>>(g, src, o, col);
+    else if (g.type == GRID_CYLINDRICAL) k_source_columns<GRID_CYLINDRICAL><<<blocks, 128, 0, s>>>(g, src, o, col);
     else k_source_columns<GRID_SPHERICAL><<<blocks, 128, 0, s>>>(g, src, o, col);
     return cudaGetLastError();
 }
@@ -135,6 +136,7 @@ cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cud
     ll.block = 256;
     *launched += 1;
     if (job.grid.type == GRID_CARTESIAN) return launch_persistent(k_plain<GRID_CARTESIAN>, job, ll, s);
+    if (job.grid.type == GRID_CYLINDRICAL) return launch_persistent(k_plain<GRID_CYLINDRICAL>, job, ll, s);
     return launch_persistent(k_plain<GRID_SPHERICAL>, job, ll, s);
 }
 

@@ -246,6 +246,7 @@ cudaError_t run_raytrace(const DevGrid& g, const DevObs& o, RtJob J, double* hos
     J.eps4pi = *host_total / (double)J.n_rays / (4.0 * CUDART_PI);
     const int grid = (int)std::min<int64_t>((J.n_rays + 255) / 256, (int64_t)sms * 8);
     if (g.type == GRID_CARTESIAN) k_rt_rays<GRID_CARTESIAN><<<grid, 256, 0, s>>>(g, o, J);
+    else if (g.type == GRID_CYLINDRICAL) k_rt_rays<GRID_CYLINDRICAL><<<grid, 256, 0, s>>>(g, o, J);
     else k_rt_rays<GRID_SPHERICAL><<<grid, 256, 0, s>>>(g, o, J);
     dim3 sg(o.nobs, (J.nqd + 255) / 256, (unsigned)((J.n_rays + RT_CHUNK - 1) / RT_CHUNK));
     k_rt_sed<<<sg, 256, 0, s>>>(J, o.nobs);

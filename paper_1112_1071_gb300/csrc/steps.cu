@@ -78,6 +78,8 @@ cudaError_t launch_step_cell_exit(const DevGrid& g, int64_t n, const float* pos,
     if (n <= 0) return cudaSuccess;
     if (g.type == GRID_CARTESIAN)
         k_step_exit<GRID_CARTESIAN><<<blocks_for(n), 256, 0, s>>>(g, n, pos, dir, cell, dist, ex, inv_L0, L0);
+    else if (g.type == GRID_CYLINDRICAL)
+        k_step_exit<GRID_CYLINDRICAL><<<blocks_for(n), 256, 0, s>>>(g, n, pos, dir, cell, dist, ex, inv_L0, L0);
     else k_step_exit<GRID_SPHERICAL><<<blocks_for(n), 256, 0, s>>>(g, n, pos, dir, cell, dist, ex, inv_L0, L0);
     return cudaGetLastError();
 }
@@ -86,6 +88,8 @@ cudaError_t launch_step_tau(const DevGrid& g, const DevDust& d, int64_t n, const
                             const float* nu, float* tau, float inv_L0, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (g.type == GRID_CARTESIAN) k_step_tau<GRID_CARTESIAN><<<blocks_for(n), 256, 0, s>>>(g, d, n, pos, dir, nu, tau, inv_L0);
+    else if (g.type == GRID_CYLINDRICAL)
+        k_step_tau<GRID_CYLINDRICAL><<<blocks_for(n), 256, 0, s>>>(g, d, n, pos, dir, nu, tau, inv_L0);
     else k_step_tau<GRID_SPHERICAL><<<blocks_for(n), 256, 0, s>>>(g, d, n, pos, dir, nu, tau, inv_L0);
     return cudaGetLastError();
 }

@@ -72,6 +72,8 @@ _SIGS = {
     "hrt_set_stream": (C.c_int, [_vp, _vp]),
     "hrt_set_grid_cartesian": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
     "hrt_set_grid_spherical": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "hrt_set_grid_cylindrical": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "hrt_add_external_source": (C.c_int, [_vp, _vp, C.c_double, C.c_double, C.c_double]),
     "hrt_set_density": (C.c_int, [_vp, _vp, _i64]),
     "hrt_set_dust": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "hrt_add_point_source": (C.c_int, [_vp, _vp, C.c_double, C.c_double]),
@@ -210,7 +212,8 @@ class Model:
         w = [_c64(x) for x in wl.walls]
         self._keep += w
         n1, n2, n3 = (len(x) - 1 for x in w)
-        f = L.hrt_set_grid_cartesian if wl.grid_type == "cartesian" else L.hrt_set_grid_spherical
+        f = {"cartesian": L.hrt_set_grid_cartesian, "spherical": L.hrt_set_grid_spherical,
+             "cylindrical": L.hrt_set_grid_cylindrical}[wl.grid_type]
         check(self.ctx, f(self.ctx, n1, n2, n3, _ptr(w[0]), _ptr(w[1]), _ptr(w[2])))
         rho = np.ascontiguousarray(wl.rho, dtype=np.float32).reshape(-1)
         check(self.ctx, L.hrt_set_density(self.ctx, _ptr(rho), rho.size))
@@ -219,6 +222,10 @@ class Model:
         for s in wl.sources:
             x = _c64(s["pos"])
             check(self.ctx, L.hrt_add_point_source(self.ctx, _ptr(x), float(s["L"]), float(s["Teff"])))
+        for e in getattr(wl, "external_sources", []) or []:
+            c = _c64(e["center"])
+            check(self.ctx, L.hrt_add_external_source(self.ctx, _ptr(c), float(e["radius"]), float(e["L"]),
+                                                      float(e["Teff"])))
         if wl.cell_source is not None:
             Lc = _c64(wl.cell_source["L"]).reshape(-1)
             check(self.ctx, L.hrt_set_cell_source(self.ctx, _ptr(Lc), Lc.size, float(wl.cell_source["Teff"])))

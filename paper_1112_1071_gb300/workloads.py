@@ -222,7 +222,7 @@ def gaussian_random_field(n: int, slope: float, rng) -> np.ndarray:
     amp = np.zeros_like(k)
     nz = k > 0
     amp[nz] = k[nz] ** (slope / 2.0)
-    g = np.fft.irfftn(f * amp, s=(n, n, n))
+    g = np.fft.irfftn(f * amp, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g

@@ -96,8 +96,8 @@ def points_in_shell(om, n, rng, r_lo, r_hi, cos_band=None, graze=None):
 
 def grid_scale(wl):
     """L0, the unit the library scales lengths by: the largest |wall| of a Cartesian grid, the
-    outer radius of a spherical one."""
-    axes = range(3) if wl.grid_type == "cartesian" else range(1)
+    outer radius of a spherical one, the largest |R| or |z| wall of a cylindrical one."""
+    axes = {"cartesian": range(3), "spherical": range(1), "cylindrical": range(2)}[wl.grid_type]
     return max(max(abs(float(wl.walls[a][0])), abs(float(wl.walls[a][-1]))) for a in axes)
 
 

@@ -1,0 +1,105 @@
+"""Cylindrical-polar grids and external isotropic sources (Sect. 2.1.1, 2.1.2) on the GPU against
+the FP64 oracle (through the C ABI): single cell exits, whole iterations on the same Philox
+streams (lockstep), and an imaging pass whose scattered field comes from the external source."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mc as M
+from paper_1112_1071_gb300 import hrt
+from paper_1112_1071_gb300 import workloads as W
+from tests.gpu_helpers import as_device_sees, dev, random_points_in_grid, torch_cuda, workload_from_walls
+
+pytestmark = pytest.mark.gpu
+
+
+def _cyl_walls():
+    return [np.array([0.3, 0.5, 0.9, 1.4, 2.0]) * W.AU, np.array([-1.5, -0.4, 0.0, 0.3, 1.5]) * W.AU,
+            np.array([0.0, 1.0, 2.5, 4.0, 2 * math.pi])]
+
+
+@pytest.mark.parametrize("kind", ["test_grid", "disk"])
+def test_cylindrical_cell_exit_matches_oracle(kind):
+    torch = torch_cuda()
+    rng = np.random.default_rng(31)
+    if kind == "test_grid":
+        wl = workload_from_walls("cylindrical", _cyl_walls())
+        radius = 1.99 * W.AU
+    else:
+        wl = W.cylindrical_disk(n_R=40, n_z=32)
+        radius = 299 * W.AU
+    om = M.OracleModel(wl)
+    om.struct(np.zeros(om.nc, np.int32))
+    p, u, c = random_points_in_grid(om, 4000, rng, radius)
+    p32, p = as_device_sees(p, wl)
+    u = u.astype(np.float32).astype(np.float64)
+    want = np.empty(len(p))
+    want_ax = np.empty(len(p), np.int32)
+    a = np.zeros(1, np.int32)
+    d = np.zeros(1, np.int32)
+    for q in range(len(p)):
+        want[q] = M.lib().or_cell_exit(om._struct, M._ptr(p[q]), M._ptr(u[q]), M._ptr(c[q], M._ip),
+                                       M._ptr(a, M._ip), M._ptr(d, M._ip))
+        want_ax[q] = a[0] * 2 + (1 if d[0] > 0 else 0)
+    m = hrt.Model(wl)
+    dist = torch.empty(len(p), dtype=torch.float32, device="cuda")
+    ex = torch.empty(len(p), dtype=torch.int32, device="cuda")
+    pd, ud, cd = dev(p32), dev(u.astype(np.float32)), dev(c)       # held until the kernel has run
+    m.step("hrt_step_cell_exit", len(p), pd.data_ptr(), ud.data_ptr(), cd.data_ptr(), dist.data_ptr(), ex.data_ptr())
+    got = dist.cpu().numpy().astype(np.float64)
+    size = np.maximum(np.hypot(p[:, 0], p[:, 1]) * 1e-3, np.diff(wl.walls[0]).min())
+    tol = 1e-5 * np.abs(want) + 1e-5 * size + 2.4e-7 * np.linalg.norm(p, axis=1)
+    bad = np.abs(got - want) > tol
+    assert bad.mean() < 4e-3, (np.flatnonzero(bad)[:5], got[bad][:5], want[bad][:5])
+    assert (ex.cpu().numpy() == want_ax).mean() > 0.998
+
+
+def _lockstep(m, st, om, ref, median_tol=1e-4):
+    assert st["e_escaped"] + st["e_killed"] == pytest.approx(om.L_tot, rel=1e-12)
+    acc = m.absorbed()
+    seen = ref["acc"] > 0
+    rel = np.abs(acc[seen] - ref["acc"][seen]) / ref["acc"][seen]
+    assert np.median(rel) < median_tol, np.median(rel)
+    assert st["n_crossings"] == pytest.approx(ref["n_crossings"], rel=2e-3)
+
+
+@pytest.mark.parametrize("kernel", [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT])
+def test_cylindrical_disk_iterations_match_oracle(kernel):
+    wl = W.cylindrical_disk(n_R=60, n_z=48, n_packets=200_000)
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    for it in range(2):
+        st = m.run_iteration(kernel=kernel)
+        ref = om.run_iteration(nthreads=16)
+        _lockstep(m, st, om, ref)
+        dust = om.rho > 0
+        Tg = m.temperature()
+        dT = np.abs(Tg[dust] - ref["T"][dust]) / ref["T"][dust]
+        assert dT.mean() < 0.01
+
+
+@pytest.mark.parametrize("grid", ["cartesian", "spherical", "cylindrical"])
+def test_external_field_iterations_match_oracle(grid):
+    wl = W.isrf_cloud(grid, n=8, tau_550=3.0, n_packets=200_000)
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    st = m.run_iteration()
+    ref = om.run_iteration(nthreads=16)
+    _lockstep(m, st, om, ref)
+    # the external packets that miss the grid escape at once on both sides
+    assert st["n_interactions"] == pytest.approx(ref["n_interactions"], rel=2e-3)
+
+
+def test_external_field_and_cylindrical_disk_imaging_pass():
+    wl = W.cylindrical_disk(n_R=40, n_z=32, n_packets=50_000, isrf_dilution=1e-13)
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    m.run_iteration()
+    om.run_iteration(nthreads=16)
+    st = m.run_iteration(peel=1, update_temperature=0)
+    ref = om.run_iteration(peel=True, update=False, nthreads=16)
+    sed, rs = m.sed(), ref["sed"]
+    np.testing.assert_allclose(sed.sum(axis=1), rs.sum(axis=1), rtol=2e-3)
+    big = rs > 1e-3 * rs.max()
+    np.testing.assert_allclose(sed[big], rs[big], rtol=3e-2)
