@@ -18,6 +18,8 @@
  *   Sect. 2.6.2  peeling-off: at emission, scattering and re-emission every observer gets
  *              eps * p * exp(-tau_obs).
  *   Sect. 2.6.1  photon binning of escaping packets by viewing angle (escape tally).
+ *   Sect. 2.2  modified random walk in optically thick cells (the published form the paper
+ *              refers to; see the section below).
  *   Sect. 3     packets within an iteration are independent; the threaded mode splits the
  *              packet range and sums per-thread accumulators at the end of the iteration.
  * Scattering uses a Henyey-Greenstein phase function (the synthetic workloads' dust).
@@ -128,6 +130,10 @@ typedef struct {
     const double* ext_c;      /* [next][3] cm */
     const double* ext_R;      /* [next] cm */
     double L0;                /* grid scale (cm): the entry nudge of external packets is 1e-6 L0 */
+    /* modified random walk (used when or_params.mrw_gamma > 0), per cell at the temperatures the
+     * pass started from */
+    const double* mrw_k;      /* [Ncells] rho chi_tR(T): inverse transport mean free path (cm^-1) */
+    const double* mrw_kp;     /* [Ncells] Planck-mean absorption coefficient kappa_P(T) (cm^2/g) */
 } or_model;
 
 typedef struct {
@@ -143,6 +149,8 @@ typedef struct {
     int32_t nthreads;
     int32_t raytrace;         /* 1: point-source emission and dust re-emission reach the SEDs and
                                  images by raytracing (Sect. 2.6.3), so they are not peeled off */
+    double mrw_gamma;         /* > 0: modified random walk where the sphere to the nearest wall is at
+                                 least mrw_gamma transport mean free paths in radius (Sect. 2.2) */
 } or_params;
 
 typedef struct {
@@ -154,6 +162,7 @@ typedef struct {
     int64_t n_interactions, n_scatter, n_absorb, n_crossings, n_peel_crossings, n_killed;
     int64_t* visits;          /* [Ncells] packet entries (runs of one packet's consecutive deposits in
                                  the cell): how many packets sampled the cell's estimate (App. A) */
+    int64_t n_mrw;            /* modified-random-walk steps */
 } or_result;
 
 #define N_ESC_MU 10
@@ -885,6 +894,95 @@ int or_raytrace_rays(const or_model* m, const or_params* P, int64_t n_rays, cons
     return 0;
 }
 
+/* ------------------------------------------------------------------ modified random walk
+ * Sect. 2.2: deep inside a cell of large optical depth, a packet crosses a sphere that lies
+ * inside the cell in one step from the diffusion approximation, instead of the many
+ * absorptions and scatterings it would take there.  The paper states the idea and refers to its
+ * published form (Min et al. 2009, with the variant of Robitaille 2010); what the steps below
+ * compute is that form:
+ *   a packet starting at the centre of a sphere of radius R0 with constant density, diffusing
+ *   with coefficient D = 1 / (3 rho chi) per unit path length, is still inside after path length
+ *   s with probability P(s) = 2 sum_{n>=1} (-1)^{n+1} exp(-n^2 pi^2 D s / R0^2);
+ *   s is drawn from P, the packet deposits eps kappa_P s (Eq. 2 with the Planck-mean absorption
+ *   coefficient of the thermalised field) and leaves from a point uniform on the sphere,
+ *   re-emitted isotropically with a frequency from the cell's emissivity row.
+ * chi is the Rosseland mean of the transport extinction chi_nu (1 - albedo g), the
+ * diffusion coefficient of anisotropically scattering dust. */
+
+#define MRW_SHRINK 0.99      /* sphere radius / distance to the nearest wall */
+#define MRW_POLE_TOL 1e-12   /* theta walls within this of 0 or pi are the polar axis */
+
+/* Distance from p (inside cell c) to the nearest wall bounding c: planes of a Cartesian cell;
+ * spheres, cones and half-planes of a spherical-polar cell; cylinders, planes and half-planes of
+ * a cylindrical cell.  The polar axis (theta = 0 or pi), r = 0 and R = 0 bound nothing (the
+ * cell continues through them), nor do the phi walls of a grid with a single phi cell.  The
+ * distance to a cone or half-plane is r sin(angle) within a quarter turn, else the distance to
+ * its edge (the origin or the axis). */
+double or_wall_distance(const or_model* m, const double p[3], const int32_t c[3]) {
+    double d = INFINITY;
+    if (m->gtype == 0) {
+        for (int a = 0; a < 3; ++a) {
+            d = fmin(d, p[a] - m->w[a][c[a]]);
+            d = fmin(d, m->w[a][c[a] + 1] - p[a]);
+        }
+        return d;
+    }
+    const double R = sqrt(p[0] * p[0] + p[1] * p[1]);
+    if (m->n[2] > 1) {
+        const double ph = wrap_phi(atan2(p[1], p[0]));
+        const double a1 = fabs(ph - m->w[2][c[2]]), a2 = fabs(m->w[2][c[2] + 1] - ph);
+        d = fmin(d, a1 < 0.5 * OR_PI ? R * sin(a1) : R);
+        d = fmin(d, a2 < 0.5 * OR_PI ? R * sin(a2) : R);
+    }
+    const double lo = m->w[0][c[0]], hi = m->w[0][c[0] + 1];
+    if (m->gtype == 1) {
+        const double r = sqrt(dot3(p, p));
+        if (lo > 0) d = fmin(d, r - lo);
+        d = fmin(d, hi - r);
+        const double th = atan2(R, p[2]);
+        const double t0 = m->w[1][c[1]], t1 = m->w[1][c[1] + 1];
+        if (t0 > MRW_POLE_TOL) {
+            const double a = fabs(th - t0);
+            d = fmin(d, a < 0.5 * OR_PI ? r * sin(a) : r);
+        }
+        if (t1 < OR_PI - MRW_POLE_TOL) {
+            const double a = fabs(t1 - th);
+            d = fmin(d, a < 0.5 * OR_PI ? r * sin(a) : r);
+        }
+    } else {
+        if (lo > 0) d = fmin(d, R - lo);
+        d = fmin(d, hi - R);
+        d = fmin(d, p[2] - m->w[1][c[1]]);
+        d = fmin(d, m->w[1][c[1] + 1] - p[2]);
+    }
+    return d;
+}
+
+/* P at x = pi^2 D s / R0^2: the alternating series summed until its terms are negligible. */
+static double mrw_survival(double x) {
+    if (!(x > 0)) return 1.0;
+    double sum = 0.0;
+    for (int n = 1;; ++n) {
+        const double t = exp(-(double)n * (double)n * x);
+        sum += (n & 1) ? t : -t;
+        if (t < 1e-20) break;
+    }
+    return 2.0 * sum;
+}
+
+/* Path length s / R0 at which P(s) = zeta, for a sphere of tau0 = rho chi R0 transport mean free
+ * paths in radius (bisection on x; s = 3 tau0 R0 x / pi^2).  zeta = 1 gives 0. */
+double or_mrw_path(double tau0, double zeta) {
+    if (zeta >= 1.0) return 0.0;
+    double lo = 0.0, hi = 1.0;
+    while (mrw_survival(hi) > zeta) hi *= 2.0;
+    for (int k = 0; k < 200 && hi - lo > 1e-16 * hi; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (mrw_survival(mid) > zeta) lo = mid; else hi = mid;
+    }
+    return 3.0 * tau0 * (0.5 * (lo + hi)) / (OR_PI * OR_PI);
+}
+
 /* ------------------------------------------------------------------ one packet history */
 static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_result* R) {
     rng_t rng;
@@ -953,6 +1051,31 @@ static void run_packet(const or_model* m, const or_params* P, int64_t pid, or_re
     dust_at(m, nu, &chi, &alb);
     int64_t nint = 0;
     for (;;) {
+        /* modified random walk: steps while the packet sits deep enough in a thick cell; each
+         * counts as one interaction against the cap */
+        while (P->mrw_gamma > 0) {
+            const int64_t ci = cell_index(m, c);
+            if (!(m->rho[ci] > 0)) break;
+            const double R0 = MRW_SHRINK * or_wall_distance(m, p, c);
+            const double tau0 = m->mrw_k[ci] * R0;
+            if (!(tau0 >= P->mrw_gamma)) break;
+            nint++;
+            if (nint > P->max_interactions) { R->e_killed += eps; R->n_killed++; return; }
+            R->n_mrw++;
+            /* the packet cannot reach the surface along a path shorter than R0 */
+            const double s = R0 * fmax(or_mrw_path(tau0, uniform(&rng)), 1.0);
+            R->acc[ci] += eps * m->mrw_kp[ci] * s;
+            if (run != ci) { R->visits[ci]++; run = ci; }
+            double n[3], u1 = uniform(&rng), u2 = uniform(&rng);
+            or_isotropic(u1, u2, n);
+            for (int a = 0; a < 3; ++a) p[a] += R0 * n[a];
+            u1 = uniform(&rng);
+            u2 = uniform(&rng);
+            or_isotropic(u1, u2, u);
+            nu = or_sample_table(m->nnu, m->nu, m->cdf_emit + (int64_t)m->emit_row[ci] * m->nnu, uniform(&rng));
+            dust_at(m, nu, &chi, &alb);
+            if (P->peel && !P->raytrace) peel(m, p, c, u, nu, eps, PEEL_REEMIT, R);
+        }
         double tau = -log(uniform(&rng));
         double dep = eps * (1.0 - alb) * chi;   /* eps * kappa_nu */
         if (walk_to_tau(m, p, u, c, tau, chi, dep, R->acc, R->visits, &run, &R->n_crossings)) {
@@ -1050,6 +1173,7 @@ int or_run_packets(const or_model* m, const or_params* P, or_result* R) {
         R->n_crossings += r->n_crossings;
         R->n_peel_crossings += r->n_peel_crossings;
         R->n_killed += r->n_killed;
+        R->n_mrw += r->n_mrw;
         free(r->acc); free(r->sed); free(r->img); free(r->esc); free(r->visits);
     }
     free(sh);

@@ -68,6 +68,7 @@ class ORModel(C.Structure):
         ("img_nx", C.c_int32), ("img_ny", C.c_int32), ("nimg", C.c_int32),
         ("img_half", C.c_double), ("img_bin", _ip),
         ("next", C.c_int32), ("ext_c", _dp), ("ext_R", _dp), ("L0", C.c_double),
+        ("mrw_k", _dp), ("mrw_kp", _dp),
     ]
 
 
@@ -76,7 +77,7 @@ class ORParams(C.Structure):
         ("n_packets", C.c_int64), ("first_packet", C.c_int64), ("key", C.c_uint32 * 2),
         ("iter_key", C.c_uint32), ("model_key", C.c_uint32), ("eps", C.c_double),
         ("max_interactions", C.c_int64), ("peel", C.c_int32), ("terminate_on_absorb", C.c_int32),
-        ("nthreads", C.c_int32), ("raytrace", C.c_int32),
+        ("nthreads", C.c_int32), ("raytrace", C.c_int32), ("mrw_gamma", C.c_double),
     ]
 
 
@@ -86,7 +87,7 @@ class ORResult(C.Structure):
         ("e_escaped", C.c_double), ("e_killed", C.c_double), ("e_absorbed", C.c_double),
         ("n_interactions", C.c_int64), ("n_scatter", C.c_int64), ("n_absorb", C.c_int64),
         ("n_crossings", C.c_int64), ("n_peel_crossings", C.c_int64), ("n_killed", C.c_int64),
-        ("visits", _lp),
+        ("visits", _lp), ("n_mrw", C.c_int64),
     ]
 
 
@@ -117,6 +118,10 @@ def _declare(L):
     L.or_tau_to_edge.restype = C.c_double
     L.or_sed_bin.argtypes = [C.POINTER(ORModel), C.c_double]
     L.or_sed_bin.restype = C.c_int
+    L.or_wall_distance.argtypes = [C.POINTER(ORModel), _dp, _ip]
+    L.or_wall_distance.restype = C.c_double
+    L.or_mrw_path.argtypes = [C.c_double, C.c_double]
+    L.or_mrw_path.restype = C.c_double
     L.or_run_packets.argtypes = [C.POINTER(ORModel), C.POINTER(ORParams), C.POINTER(ORResult)]
     L.or_run_packets.restype = C.c_int
 
@@ -261,17 +266,38 @@ class OracleModel:
         m.ext_c = _ptr(self.ext_c) if self.next else None
         m.ext_R = _ptr(self.ext_R) if self.next else None
         m.L0 = self.L0
+        m.mrw_k = _ptr(self._mrw_k) if getattr(self, "_mrw_k", None) is not None else None
+        m.mrw_kp = _ptr(self._mrw_kp) if getattr(self, "_mrw_kp", None) is not None else None
         self._struct = m
         return m
 
+    def mrw_tables(self):
+        """Transport Rosseland mean extinction and Planck-mean absorption coefficient on the
+        temperature nodes (the modified random walk, Sect. 2.2)."""
+        if getattr(self, "_mrw_nodes", None) is None:
+            self._mrw_nodes = (T.transport_rosseland_mean(self.nu, self.chi, self.albedo, self.wl.g, self.T_nodes),
+                               T.planck_mean_kappa(self.nu, T.kappa_abs(self.chi, self.albedo), self.T_nodes))
+        return self._mrw_nodes
+
+    def set_mrw_cells(self, T_cells):
+        """Per-cell rho chi_tR(T) and kappa_P(T) (log-log between the temperature nodes) at the
+        temperatures a pass starts from."""
+        chi_t, kp = self.mrw_tables()
+        self._mrw_k = np.ascontiguousarray(self.rho * T.interp_loglog(T_cells, self.T_nodes, chi_t))
+        self._mrw_kp = np.ascontiguousarray(T.interp_loglog(T_cells, self.T_nodes, kp))
+
     # ---------------------------------------------------------------- packets
     def run_packets(self, n_packets, iter_key, peel=False, max_interactions=1_000_000,
-                    terminate_on_absorb=False, nthreads=1, first_packet=0, n_total=None, raytrace=False):
+                    terminate_on_absorb=False, nthreads=1, first_packet=0, n_total=None, raytrace=False,
+                    mrw_gamma=0.0):
         """Propagate packets first_packet .. first_packet+n_packets-1 with the temperatures held
         now; eps = L_tot / n_total (dt = 1 s).  With raytrace, point-source emission and dust
-        re-emission are not peeled off (they reach the SEDs by raytracing, Sect. 2.6.3)."""
+        re-emission are not peeled off (they reach the SEDs by raytracing, Sect. 2.6.3).
+        mrw_gamma > 0 turns the modified random walk on (Sect. 2.2)."""
         n_total = n_packets if n_total is None else n_total
         emit_row = T.emission_row(self.T, self.T_nodes)
+        if mrw_gamma > 0:
+            self.set_mrw_cells(self.T)
         m = self.struct(emit_row)
         P = ORParams()
         P.n_packets = int(n_packets)
@@ -285,6 +311,7 @@ class OracleModel:
         P.terminate_on_absorb = int(bool(terminate_on_absorb))
         P.nthreads = int(nthreads)
         P.raytrace = int(bool(raytrace))
+        P.mrw_gamma = float(mrw_gamma)
         acc = np.zeros(self.nc)
         sed = np.zeros(max(1, self.nobs * self.wl.nsed))
         img = np.zeros(max(1, self.nobs * self.nimg * self.wl.img_nx * self.wl.img_ny))
@@ -300,7 +327,8 @@ class OracleModel:
                    esc=esc.reshape(N_ESC_MU, self.wl.nsed), eps=P.eps,
                    e_escaped=R.e_escaped, e_killed=R.e_killed, e_absorbed=R.e_absorbed,
                    n_interactions=R.n_interactions, n_scatter=R.n_scatter, n_absorb=R.n_absorb,
-                   n_crossings=R.n_crossings, n_peel_crossings=R.n_peel_crossings, n_killed=R.n_killed)
+                   n_crossings=R.n_crossings, n_peel_crossings=R.n_peel_crossings, n_killed=R.n_killed,
+                   n_mrw=R.n_mrw)
         if self.nimg:
             out["img"] = img.reshape(self.nobs, self.nimg, self.wl.img_ny, self.wl.img_nx)
         return out
@@ -313,14 +341,16 @@ class OracleModel:
 
     # ---------------------------------------------------------------- iteration
     def run_iteration(self, n_packets=None, p=0.99, quantity="T", peel=False, update=True,
-                      max_interactions=1_000_000, terminate_on_absorb=False, nthreads=1, pda_min=0):
+                      max_interactions=1_000_000, terminate_on_absorb=False, nthreads=1, pda_min=0,
+                      mrw_gamma=0.0):
         """One Lucy iteration (update=True) or one imaging pass (update=False).  pda_min > 0
         (spherical grids): cells with dust sampled by fewer than pda_min packet path segments
-        take their temperature from the partial diffusion approximation (App. A)."""
+        take their temperature from the partial diffusion approximation (App. A).  mrw_gamma > 0:
+        modified random walk in thick cells (Sect. 2.2)."""
         n = self.wl.n_packets if n_packets is None else int(n_packets)
         key = self.iteration if update else (IMAGING_KEY | self.iteration)
         out = self.run_packets(n, key, peel=peel, max_interactions=max_interactions,
-                               terminate_on_absorb=terminate_on_absorb, nthreads=nthreads)
+                               terminate_on_absorb=terminate_on_absorb, nthreads=nthreads, mrw_gamma=mrw_gamma)
         if update:
             adot = out["acc"] / (self.vol * 1.0)                     # Eq. 2, dt = 1 s
             Tn, _, _ = T.temperature_from_adot(adot, self.T_nodes, self.dust.E)     # Eq. 3

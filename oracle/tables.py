@@ -52,6 +52,24 @@ def rosseland_mean(nu, chi, T_nodes):
     return trapezoid_pieces(nu, w).sum(axis=-1) / trapezoid_pieces(nu, w / chi[None, :]).sum(axis=-1)
 
 
+def transport_rosseland_mean(nu, chi, albedo, g, T_nodes):
+    """Rosseland mean of the transport extinction chi_nu (1 - albedo_nu g) (Henyey-Greenstein
+    scattering removes only the share 1 - g of the momentum): the diffusion coefficient
+    D = 1 / (3 rho chi) of the modified random walk (Sect. 2.2)."""
+    chi_t = np.asarray(chi, dtype=np.float64) * (1.0 - np.asarray(albedo, dtype=np.float64) * float(g))
+    return rosseland_mean(nu, chi_t, T_nodes)
+
+
+def planck_mean_kappa(nu, kappa, T_nodes):
+    """Planck-mean absorption coefficient int kappa_nu B_nu dnu / int B_nu dnu over the dust
+    nodes (trapezoid rule): the absorption per unit path length of a field thermalised at T."""
+    nu = np.asarray(nu, dtype=np.float64)
+    T_nodes = np.asarray(T_nodes, dtype=np.float64)
+    b = planck_bnu(nu[None, :], T_nodes[:, None])
+    kb = np.asarray(kappa, dtype=np.float64)[None, :] * b
+    return trapezoid_pieces(nu, kb).sum(axis=-1) / trapezoid_pieces(nu, b).sum(axis=-1)
+
+
 def interp_loglog(x, x_nodes, y_nodes):
     """y(x) linear in log-log between table nodes, clamped to the end values."""
     lx = np.log(np.asarray(x_nodes, dtype=np.float64))
