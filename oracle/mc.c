@@ -506,7 +506,8 @@ static int cyl_locate(const or_model* m, const double p[3], const double u[3], i
     }
     c[2] = k;
     if (R < Rw[0] || (R == Rw[0] && Rw[0] > 0 && !(vR > 0))) { c[0] = -1; return 1; }
-    int i = locate_axis(Rw, m->n[0], R, vR);
+    /* without a hole the axis R = 0 lies inside the innermost ring (it is not a wall) */
+    int i = (R == 0.0 && Rw[0] == 0.0) ? 0 : locate_axis(Rw, m->n[0], R, vR);
     if (i < 0) return -1;
     c[0] = i;
     return 0;

@@ -558,7 +558,8 @@ __device__ __forceinline__ bool cyl_locate(const DevGrid& g, Ray& r) {
     const float vR = r.p.x * r.u.x + r.p.y * r.u.y;
     const float R0 = __ldg(g.rw);
     if (R0 > 0.f && (R < R0 || (R == R0 && !(vR > 0.f)))) return !cyl_cross_hole(g, r);
-    const int i = locate_axis(g.rw, g.n1, R, vR);
+    // without a hole the axis R = 0 lies inside the innermost ring (it is not a wall)
+    const int i = (R == 0.f && R0 == 0.f) ? 0 : locate_axis(g.rw, g.n1, R, vR);
     if (i < 0) return false;
     r.i = i;
     r.j = j;

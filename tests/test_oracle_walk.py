@@ -187,6 +187,25 @@ def test_locate_on_walls_follows_direction():
         assert st == 0 and tuple(c) == want
 
 
+def test_axis_of_a_cylindrical_grid_without_hole_is_inside_the_first_ring():
+    # R = 0 bounds no cell when R_0 = 0: a source on the axis starts in ring 0 whatever its
+    # direction, and walks out of it as a ray from the axis (the first wall is R_1)
+    walls = [np.array([0.0, 1.0, 2.0]) * W.AU, np.array([-1.0, 0.5, 1.0]) * W.AU, np.array([0.0, 2 * math.pi])]
+    om = _model("cylindrical", walls)
+    out = np.zeros(3)
+    c = np.zeros(3, np.int32)
+    for u in ((1.0, 0.0, 0.0), (0.0, 0.6, 0.8), (0.0, 0.0, -1.0)):
+        u = np.asarray(u)
+        st = M.lib().or_locate(om._struct, M._ptr(np.zeros(3)), M._ptr(u), M._ptr(out), M._ptr(c, M._ip))
+        assert st == 0 and tuple(c) == (0, 0, 0)
+        ax, d = np.zeros(1, np.int32), np.zeros(1, np.int32)
+        dist = M.lib().or_cell_exit(om._struct, M._ptr(np.zeros(3)), M._ptr(u), M._ptr(c, M._ip), M._ptr(ax, M._ip),
+                                    M._ptr(d, M._ip))
+        R_hit = W.AU / math.hypot(u[0], u[1]) if math.hypot(u[0], u[1]) > 0 else math.inf
+        z_hit = (0.5 * W.AU / u[2] if u[2] > 0 else -W.AU / u[2]) if u[2] != 0 else math.inf
+        assert dist == pytest.approx(min(R_hit, z_hit), rel=1e-12)
+
+
 def _brute_cyl(walls, p, u):
     Rw, zw, pw = (np.asarray(w, float) for w in walls)
     a = u[0] ** 2 + u[1] ** 2
