@@ -168,6 +168,20 @@ typedef struct {
                                     proportion to the cells' emission m E(T), each carrying
                                     L_dust / raytrace_rays over all bins at once; scattered light is
                                     still peeled off.  0 (default) = off; < 2^32 */
+    double mrw_gamma;            /* modified random walk (Sect. 2.2, in the published diffusion form the
+                                    paper refers to): > 0 lets a packet in a cell with dust cross, in
+                                    one step, the sphere of radius 0.99 x its distance to the nearest
+                                    wall of the cell whenever that sphere is at least mrw_gamma
+                                    transport mean free paths (1 / rho chi_t, chi_t the Rosseland mean
+                                    of chi_nu (1 - albedo g) at the cell's temperature) in radius.
+                                    The step's path length s solves the diffusion survival probability
+                                    (at least the radius), deposits kappa_P(T) s (Eq. 2 with the
+                                    Planck-mean absorption coefficient), and ends with an isotropic
+                                    re-emission from a point uniform on the sphere (frequency from the
+                                    cell's emissivity row; peeled off like a re-emission); each step
+                                    counts as one interaction against max_interactions.  Single-model
+                                    runs only (a batch returns HRT_EINVAL).  0 (default) = off;
+                                    finite, >= 0 */
 } hrt_run_params;
 
 typedef struct {
@@ -187,6 +201,7 @@ typedef struct {
     int64_t n_pda;               /* cells whose T came from the diffusion approximation */
     int64_t pda_iterations;      /* conjugate-gradient iterations of its solve */
     double pda_residual;         /* |b - A x| / |b| at the end of the solve */
+    int64_t n_mrw;               /* modified-random-walk steps */
 } hrt_iter_stats;
 
 /* Defaults: max_interactions 1e6, peel 0, update_temperature 1, p 0.99, q_thres 1.02 on T,
@@ -241,6 +256,16 @@ int hrt_step_cell_exit(hrt_ctx* ctx, int64_t n, const float* d_pos, const float*
  * (the peel-off ray of Sect. 2.6.2). */
 int hrt_step_tau_to_edge(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir,
                          const float* d_nu, float* d_tau);
+
+/* Modified random walk (Sect. 2.2): distance (cm) from pos [n][3] (cm, inside cell [n][3]) to
+ * the nearest wall bounding the cell; the polar axis, r = 0, R = 0 and the phi walls of a
+ * single-phi-cell grid bound nothing. */
+int hrt_step_wall_distance(hrt_ctx* ctx, int64_t n, const float* d_pos, const int32_t* d_cell, float* d_dist);
+
+/* Modified random walk (Sect. 2.2): path length / R0 at which the diffusion survival probability
+ * 2 sum_{n>=1} (-1)^{n+1} exp(-n^2 pi^2 s / (3 tau0 R0)) equals zeta[n] in (0, 1], for spheres of
+ * tau0[n] transport mean free paths in radius (0 for zeta = 1; no lower bound applied). */
+int hrt_step_mrw_path(int64_t n, const float* d_tau0, const float* d_zeta, float* d_out, void* stream);
 
 /* Henyey-Greenstein scattering: new direction from dir_in [n][3] and uniforms u1 (cos theta)
  * and u2 (azimuth). */

@@ -165,6 +165,7 @@ int stage_grid(hrt_ctx* ctx) {
         // sin(theta) < 0.1 cost 1.3x in walk time, with no change in the parity tests.
         g.r_fp64 = (float)(rwd[1] * (1.0 + 1e-6));
         g.sin_fp64 = 0.02f;
+        g.poles = (ctx->w[1][0] <= 1e-12 ? 1 : 0) | (ctx->w[1][nt] >= M_PI - 1e-12 ? 2 : 0);
         for (int i = 0; i < nr; ++i) va[i] = (std::pow(ctx->w[0][i + 1], 3) - std::pow(ctx->w[0][i], 3)) / 3.0;
         for (int j = 0; j < nt; ++j) vb[j] = std::cos(ctx->w[1][j]) - std::cos(ctx->w[1][j + 1]);
         for (int k = 0; k < np; ++k) vc[k] = ctx->w[2][k + 1] - ctx->w[2][k];
@@ -222,6 +223,12 @@ int stage_dust(hrt_ctx* ctx) {
     CK(ctx->d_lnchiR.alloc(nT), "tables");
     CK(launch_rosseland(nnu, ctx->d_nu.p, ctx->d_chid.p, nT, ctx->d_Tn.p, ctx->d_chiR.p, ctx->d_lnchiR.p, s),
        "rosseland table");
+    CK(ctx->d_albd.upload(ctx->alb.data(), nnu, s), "dust");
+    CK(ctx->d_mrw_lnchit.alloc(nT), "tables");
+    CK(ctx->d_mrw_lnkp.alloc(nT), "tables");
+    CK(launch_mrw_tables(nnu, ctx->d_nu.p, ctx->d_chid.p, ctx->d_kappa.p, ctx->d_albd.p, ctx->g, nT, ctx->d_Tn.p,
+                         ctx->d_mrw_lnchit.p, ctx->d_mrw_lnkp.p, s),
+       "mrw tables");
     DevDust& d = ctx->dust;
     d.nnu = nnu; d.nT = nT;
     d.lnu = ctx->d_lnu.p; d.inv_dlnu = ctx->d_inv_dlnu.p; d.lchi = ctx->d_lchi.p; d.alb = ctx->d_alb.p;
@@ -418,8 +425,10 @@ int hrt_destroy(hrt_ctx* ctx) {
                     &ctx->d_kappa, &ctx->d_Tn, &ctx->d_lnT, &ctx->d_E, &ctx->d_lnE, &ctx->d_src_cdf, &ctx->d_cell_cdf,
                     &ctx->d_spec_nud, &ctx->d_teff, &ctx->d_unu, &ctx->d_uf, &ctx->d_T, &ctx->d_adot, &ctx->d_acc,
                     &ctx->d_sed, &ctx->d_img, &ctx->d_chid, &ctx->d_chiR, &ctx->d_lnchiR, &ctx->d_pgeo, &ctx->d_pda,
-                    &ctx->d_Tprev, &ctx->d_adotprev, &ctx->d_pda_scal})
+                    &ctx->d_Tprev, &ctx->d_adotprev, &ctx->d_pda_scal, &ctx->d_albd, &ctx->d_mrw_lnchit,
+                    &ctx->d_mrw_lnkp})
         b->release();
+    ctx->d_mrw_k.release(); ctx->d_mrw_kp.release();
     ctx->d_visits.release(); ctx->d_pda_state.release(); ctx->d_pda_count.release(); ctx->d_pda_flag.release();
     for (auto* b : {&ctx->d_rho, &ctx->d_rt_qd_w, &ctx->d_rt_qd_chi, &ctx->d_rt_qs_w, &ctx->d_rt_qs_chi,
                     &ctx->d_rt_inv_dnu, &ctx->d_rt_col})
@@ -717,6 +726,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         return ctx->fail(HRT_EINVAL, "pda_min_visits must be in [0, 2^32)");
     if (P.raytrace_rays < 0 || P.raytrace_rays > 0xFFFFFFFFll)
         return ctx->fail(HRT_EINVAL, "raytrace_rays must be in [0, 2^32)");
+    if (!(P.mrw_gamma >= 0) || !std::isfinite(P.mrw_gamma))
+        return ctx->fail(HRT_EINVAL, "mrw_gamma must be finite and >= 0");
     const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
     if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
         return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");
@@ -732,6 +743,16 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     // have been set since the last update)
     CK(launch_emit_rows(ctx->d_T.p, ctx->d_row.p, nc, ctx->d_lnT.p, (int)ctx->Tn.size(), s), "emission rows");
     launched++;
+    const bool mrw = P.mrw_gamma > 0;
+    if (mrw) {
+        // modified random walk coefficients at the same temperatures
+        CK(ctx->d_mrw_k.alloc(nc), "alloc mrw");
+        CK(ctx->d_mrw_kp.alloc(nc), "alloc mrw");
+        CK(launch_mrw_cells(nc, ctx->grid.rhoL, ctx->d_T.p, ctx->d_lnT.p, ctx->d_mrw_lnchit.p, ctx->d_mrw_lnkp.p,
+                            (int)ctx->Tn.size(), ctx->d_mrw_k.p, ctx->d_mrw_kp.p, s),
+           "mrw coefficients");
+        launched++;
+    }
     if (P.peel) {
         CK(cudaMemsetAsync(ctx->d_sed.p, 0, ctx->d_sed.n * sizeof(double), s), "zero sed");
         CK(cudaMemsetAsync(ctx->d_img.p, 0, ctx->d_img.n * sizeof(double), s), "zero image");
@@ -780,6 +801,9 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     const bool raytrace = A.peel && !P.update_temperature && P.raytrace_rays > 0;
     A.rt = raytrace ? 1 : 0;
     A.terminate_on_absorb = P.terminate_on_absorb;
+    A.mrw_gamma = mrw ? (float)P.mrw_gamma : 0.f;
+    A.mrw_k = mrw ? ctx->d_mrw_k.p : nullptr;
+    A.mrw_kp = mrw ? ctx->d_mrw_kp.p : nullptr;
     A.budget_ns = P.watchdog_ms > 0 ? (uint64_t)(P.watchdog_ms * 1e6) : 0ull;
     A.smem_sed = (size_t)ctx->obs.nobs * ctx->obs.nsed * 8 + (size_t)N_ESC_MU * ctx->obs.nsed * 4 <= 96 * 1024;
     A.work_counter = ctx->d_work.p;
@@ -982,6 +1006,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     st.ms_total = ms;
     st.kernel_launches = launched;
     st.n_pda = pda_stats.n_cells;
+    st.n_mrw = (int64_t)h[C_MRW];
     st.pda_iterations = pda_stats.iterations;
     st.pda_residual = pda_stats.residual;
     if (P.update_temperature) ctx->visits_valid = pda;
@@ -1156,6 +1181,25 @@ int hrt_step_cell_exit(hrt_ctx* ctx, int64_t n, const float* d_pos, const float*
        "cell exit");
     CK(cudaStreamSynchronize(ctx->stream), "cell exit");
     return HRT_OK;
+}
+
+int hrt_step_wall_distance(hrt_ctx* ctx, int64_t n, const float* d_pos, const int32_t* d_cell, float* d_dist) {
+    int rc = step_prepare(ctx);
+    if (rc != HRT_OK) return rc;
+    if (n < 0 || (n > 0 && (!d_pos || !d_cell || !d_dist))) return ctx->fail(HRT_EINVAL, "wall distance: bad arguments");
+    DeviceGuard dg(ctx->device);
+    CK(launch_step_wall_distance(ctx->grid, n, d_pos, d_cell, d_dist, (float)(1.0 / ctx->L0), (float)ctx->L0,
+                                 ctx->stream),
+       "wall distance");
+    CK(cudaStreamSynchronize(ctx->stream), "wall distance");
+    return HRT_OK;
+}
+
+int hrt_step_mrw_path(int64_t n, const float* d_tau0, const float* d_zeta, float* d_out, void* stream) {
+    if (n < 0 || (n > 0 && (!d_tau0 || !d_zeta || !d_out))) return HRT_EINVAL;
+    cudaError_t e = launch_step_mrw_path(n, d_tau0, d_zeta, d_out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? HRT_OK : HRT_ECUDA;
 }
 
 int hrt_step_tau_to_edge(hrt_ctx* ctx, int64_t n, const float* d_pos, const float* d_dir, const float* d_nu, float* d_tau) {

@@ -101,6 +101,8 @@ struct hrt_ctx {
     DBuf<double> d_rwd, d_cthd, d_sthd, d_va, d_vb, d_vc;
     DBuf<float> d_lnu, d_inv_dlnu, d_lchi, d_alb, d_nuf, d_cdf_emit;
     DBuf<double> d_nu, d_kappa, d_Tn, d_lnT, d_E, d_lnE;
+    DBuf<double> d_albd, d_mrw_lnchit, d_mrw_lnkp;   // albedo (FP64); MRW node tables
+    DBuf<float> d_mrw_k, d_mrw_kp;                   // MRW per-cell coefficients of the current pass
     DBuf<float> d_src_pos, d_spec_nu, d_spec_cdf;
     DBuf<double> d_src_cdf, d_cell_cdf, d_spec_nud, d_teff, d_unu, d_uf;
     DBuf<int> d_uoff, d_un;

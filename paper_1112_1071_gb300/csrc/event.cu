@@ -22,7 +22,7 @@
 
 namespace hrt {
 
-enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE };
+enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE, M_MRW };
 
 // Optical depth beyond which a peel-off ray stops: exp(-40) = 4e-18 of its weight remains.
 constexpr float PEEL_TAU_STOP = 40.f;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v)
 
 // The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
 // `need` (ballot) lanes want a packet and returns this lane's packet id, or -1 when none is left.
-template <int G, bool WAGG, bool PEEL, class Fetch>
+template <int G, bool WAGG, bool PEEL, bool MRW, class Fetch>
 __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, const DevSources& s, const DevObs& o,
                                            const RunArgs& a, const Tallies& t, const SharedTallies& st,
                                            LocalCounters& lc, Fetch&& fetch) {
@@ -88,6 +88,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     bool aborted = false;
 
     auto start_walk = [&]() {
+        if constexpr (MRW) {
+            if (a.mrw_gamma > 0.f) {       // the event phase tries modified-random-walk steps first
+                mode = M_MRW;
+                return;
+            }
+        }
         tau = -logf(pk.rng.next());
         ray_steps = 0;
         zero_run = 0;
@@ -186,6 +192,46 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         } while (mode == M_PEEL_DONE);
     };
 
+    // modified random walk (Sect. 2.2): steps while the packet sits deep in a thick cell, each one
+    // interaction against the cap and an isotropic re-emission at its end (peeled off like one);
+    // then a new flight
+    auto mrw_steps = [&]() {
+        // modified random walk (Sect. 2.2): steps while the packet sits deep in a thick cell,
+        // each one interaction against the cap and an isotropic re-emission at its end (peeled
+        // off like one); then a new flight
+        for (;;) {
+            const float R0 = mrw_sphere<G>(g, a, pk.r);
+            if (R0 < 0.f) {
+                tau = -logf(pk.rng.next());
+                ray_steps = 0;
+                zero_run = 0;
+                mode = M_WALK;
+                break;
+            }
+            if (++pk.nint > a.max_interactions) {
+                lc.v[C_KILLED]++;
+                end_packet();
+                break;
+            }
+            lc.v[C_MRW]++;
+            const float v = mrw_take(d, o, a, pk, R0);
+            if (pk.r.ci == dep_ci) {
+                dep_val += v;
+            } else {
+                flush_run(t, dep_ci, dep_val);
+                dep_ci = pk.r.ci;
+                dep_val = v;
+            }
+            porg = pk.r.p;
+            if constexpr (PEEL) {
+                if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !a.rt) {
+                    after_event(PEEL_ISO, 0, true);
+                    break;
+                }
+            }
+        }
+    };
+
     for (;;) {
         // ------------------------------------------------------------ event phase
         if (mode == M_KILLED) {
@@ -227,6 +273,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         } else if (PEEL && mode == M_PEEL_DONE) {
             finish_peels();
         }
+        if (MRW && mode == M_MRW) mrw_steps();
         // refill: lanes without a packet take the next ids
         const unsigned need = __ballot_sync(FULL, mode == M_NEED);
         if (need) {
@@ -245,6 +292,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     porg = pk.last_origin;
                     after_event(PEEL_ISO, pk.emit_relocate, pk.src < s.npoint);
                 }
+                if (MRW && mode == M_MRW) mrw_steps();
             }
         }
         const unsigned live = __ballot_sync(FULL, mode != M_DONE);
@@ -333,7 +381,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
 // ---------------------------------------------------------------- one model
 // MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80);
 // PEEL = imaging pass (peel-off rays walked), compiled out of the Lucy iterations' kernel.
-template <int G, bool WAGG, int MINB, bool PEEL>
+template <int G, bool WAGG, int MINB, bool PEEL, bool MRW>
 __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
     const SharedTallies st = shared_tallies(o, a);
     LocalCounters lc;
@@ -347,15 +395,17 @@ __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSo
         const unsigned long long q = base + __popc(need & lt_mask);
         return q < (unsigned long long)a.n_packets ? (long long)(a.first_packet + (int64_t)q) : -1ll;
     };
-    event_loop<G, WAGG, PEEL>(g, d, s, o, a, t, st, lc, fetch);
+    event_loop<G, WAGG, PEEL, MRW>(g, d, s, o, a, t, st, lc, fetch);
     flush_counters(lc, t.counters);
     flush_shared(o, a, t, st);
 }
 
+// MRW = modified random walk compiled in (runs with mrw_gamma > 0; 3 blocks per SM only)
 template <int G, bool PEEL>
 static cudaError_t launch_event_shape(const PropagateJob& j, const Launch& l, int bps, cudaStream_t s) {
-    if (bps >= 3) return launch_persistent(k_event<G, true, 3, PEEL>, j, l, s);
-    return launch_persistent(k_event<G, true, 2, PEEL>, j, l, s);
+    if (j.args.mrw_gamma > 0.f) return launch_persistent(k_event<G, true, 3, PEEL, true>, j, l, s);
+    if (bps >= 3) return launch_persistent(k_event<G, true, 3, PEEL, false>, j, l, s);
+    return launch_persistent(k_event<G, true, 2, PEEL, false>, j, l, s);
 }
 
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched) {
@@ -411,7 +461,7 @@ __global__ void __launch_bounds__(256, MINB) k_event_batch(const BatchModel* __r
         };
         LocalCounters lc;
         lc.zero();
-        event_loop<G, WAGG, false>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
+        event_loop<G, WAGG, false, false>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
         flush_counters(lc, M.t.counters);
     }
 }

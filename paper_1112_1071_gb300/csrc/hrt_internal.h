@@ -156,6 +156,12 @@ struct PdaStats {
 };
 cudaError_t launch_rosseland(int nnu, const double* nu, const double* chi, int nT, const double* T, double* chiR,
                              double* lnchiR, cudaStream_t s);
+// modified random walk (mrw.cu): FP64 node tables of ln chi_t(T) and ln kappa_P(T), then the FP32
+// per-cell coefficients rhoL chi_t(T_c) and kappa_P(T_c) a pass reads
+cudaError_t launch_mrw_tables(int nnu, const double* nu, const double* chi, const double* kappa, const double* alb,
+                              double g, int nT, const double* T, double* ln_chit, double* ln_kp, cudaStream_t s);
+cudaError_t launch_mrw_cells(int64_t n, const float* rhoL, const double* T, const double* lnT, const double* ln_chit,
+                             const double* ln_kp, int nT, float* k, float* kp, cudaStream_t s);
 cudaError_t run_pda(const PdaJob& J, double tol, int max_iter, int* host_flag, double* host_scal, PdaStats* st,
                     cudaStream_t s, int* launched);
 
@@ -172,6 +178,9 @@ cudaError_t launch_step_cell_exit(const DevGrid& g, int64_t n, const float* pos,
                                   const int32_t* cell, float* dist, int32_t* ex, float inv_L0, float L0, cudaStream_t s);
 cudaError_t launch_step_tau(const DevGrid& g, const DevDust& d, int64_t n, const float* pos, const float* dir,
                             const float* nu, float* tau, float inv_L0, cudaStream_t s);
+cudaError_t launch_step_wall_distance(const DevGrid& g, int64_t n, const float* pos, const int32_t* cell, float* dist,
+                                     float inv_L0, float L0, cudaStream_t s);
+cudaError_t launch_step_mrw_path(int64_t n, const float* tau0, const float* zeta, float* out, cudaStream_t s);
 cudaError_t launch_step_hg(float g, int64_t n, const float* din, const float* u1, const float* u2, float* dout,
                            cudaStream_t s);
 cudaError_t launch_step_sample(const float* x, const float* cdf, int nx, int64_t n, const int32_t* row,

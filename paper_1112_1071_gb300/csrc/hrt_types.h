@@ -34,7 +34,8 @@ struct DevGrid {
     float r0;                      // inner radius (scaled), 0 without a hole
     float r_fp64;                  // sphere coefficients for walls below this radius in FP64
     float sin_fp64;                // cone coefficients for walls with sin(theta) below this in FP64
-    int32_t pad0;
+    int32_t poles;                 // spherical: bit 0 theta_0 = 0, bit 1 theta_n = pi (the polar axis,
+                                   // which bounds no cell)
 };
 
 struct DevDust {
@@ -112,6 +113,7 @@ enum Counter {
     C_PACKETS_DONE,
     C_WATCHDOG,
     C_STUCK,          // rays ended after MAX_WALK_STEPS crossings without reaching an event
+    C_MRW,            // modified-random-walk steps
     N_COUNTERS
 };
 
@@ -128,7 +130,10 @@ struct RunArgs {
     int32_t peel;
     int32_t terminate_on_absorb;
     int32_t rt;                    // 1: point-source emission and re-emission are raytraced, not peeled
-    int32_t pad_rt;
+    float mrw_gamma;               // > 0: modified random walk where the sphere to the nearest wall is
+                                   // at least this many transport mean free paths in radius
+    const float* mrw_k;            // [ncells] rhoL chi_t(T): inverse transport mean free path (scaled)
+    const float* mrw_kp;           // [ncells] Planck-mean absorption coefficient kappa_P(T)
     uint64_t budget_ns;            // watchdog budget after the launch stamp, 0 = none
     int32_t regroup;               // event kernel: leave walk phase below this many walkers
     int32_t smem_sed;              // 1: SED tallies in shared memory

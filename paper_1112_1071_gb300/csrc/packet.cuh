@@ -3,6 +3,7 @@
 // absorb and re-emit, Sect. 2.2 and 2.1.3) and peeling-off (Sect. 2.6.2).
 #pragma once
 #include "device_grid.cuh"
+#include "mrw.cuh"
 
 namespace hrt {
 
@@ -241,6 +242,37 @@ __device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, con
         if (a.peel) peel_event<G>(g, d, o, a, t, sed_s, pk.r, uin, PEEL_HG, false, pk.dust.chi, pk.sbin, lc);
     }
     return true;
+}
+
+// Modified random walk (Sect. 2.2).  mrw_sphere: radius R0 of the step's sphere at the
+// packet's position (MRW_SHRINK times the distance to the nearest wall of its cell), or -1 when
+// the cell has no dust or the sphere is fewer than a.mrw_gamma transport mean free paths in
+// radius.  mrw_take: the step itself, drawing (in this order) the path length, the exit point
+// on the sphere and the isotropic re-emission (direction, then frequency from the cell's
+// emissivity row); returns the deposit kappa_P(T) s (scaled length; Eq. 2 with the Planck-mean
+// absorption coefficient of the thermalised field).  The packet stays in its cell.
+template <int G>
+__device__ __forceinline__ float mrw_sphere(const DevGrid& g, const RunArgs& a, const Ray& r) {
+    const float k = __ldg(a.mrw_k + r.ci);
+    if (!(k > 0.f)) return -1.f;
+    const float R0 = MRW_SHRINK * wall_distance<G>(g, r);
+    return (k * R0 >= a.mrw_gamma) ? R0 : -1.f;
+}
+
+__device__ __forceinline__ float mrw_take(const DevDust& d, const DevObs& o, const RunArgs& a, Packet& pk, float R0) {
+    const float tau0 = __ldg(a.mrw_k + pk.r.ci) * R0;
+    // the packet cannot reach the sphere's surface along a path shorter than R0
+    const float s = R0 * fmaxf(mrw_path(tau0, pk.rng.next()), 1.f);
+    const float u1 = pk.rng.next(), u2 = pk.rng.next();
+    const float3 n = isotropic_dir(u1, u2);
+    pk.r.p.x = fmaf(R0, n.x, pk.r.p.x);
+    pk.r.p.y = fmaf(R0, n.y, pk.r.p.y);
+    pk.r.p.z = fmaf(R0, n.z, pk.r.p.z);
+    const float u3 = pk.rng.next(), u4 = pk.rng.next();
+    set_dir(pk.r, isotropic_dir(u3, u4));
+    const int row = min(max(__ldg(d.emit_row + pk.r.ci), 0), d.nT - 1);   // bounds check
+    set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
+    return __ldg(a.mrw_kp + pk.r.ci) * s;
 }
 
 __device__ __forceinline__ void tally_escape(const DevObs& o, const Tallies& t, const Packet& pk, unsigned* esc_s) {

@@ -16,21 +16,10 @@
 // = 0 is solved for x = T^4 by Jacobi-preconditioned conjugate gradients; Adot = E(T) (Eq. 3)
 // and the convergence key of the solved cells are then replaced.
 #include "hrt_internal.h"
+#include "planck.cuh"
 #include "temperature.cuh"
 
 namespace hrt {
-
-constexpr double PDA_H = 6.62607015e-27;
-constexpr double PDA_K = 1.380649e-16;
-constexpr double PDA_C = 2.99792458e10;
-
-// dB_nu/dT = (2 h nu^3 / c^2) (x / T) / (4 sinh^2(x / 2)), x = h nu / k T.
-__device__ __forceinline__ double planck_dbdt(double nu, double T) {
-    const double x = PDA_H * nu / (PDA_K * T);
-    if (x > 1400.0) return 0.0;
-    const double s = sinh(0.5 * x);
-    return 2.0 * PDA_H * nu * nu * nu / (PDA_C * PDA_C) * (x / T) / (4.0 * s * s);
-}
 
 // Rosseland mean extinction chi_R(T_m) = int dB/dT dnu / int chi^-1 dB/dT dnu, trapezoid rule
 // over the dust nodes; one thread per temperature node.
@@ -55,21 +44,6 @@ cudaError_t launch_rosseland(int nnu, const double* nu, const double* chi, int n
                              double* lnchiR, cudaStream_t s) {
     k_rosseland<<<(nT + 127) / 128, 128, 0, s>>>(nnu, nu, chi, nT, T, chiR, lnchiR);
     return cudaGetLastError();
-}
-
-// y(x) linear in log-log on the table (lnx nodes ascending), clamped to the end values.
-__device__ __forceinline__ double loglog(double x, const double* __restrict__ lnx, const double* __restrict__ lny,
-                                         int n) {
-    const double lx = log(x);
-    if (!(lx > lnx[0])) return exp(lny[0]);
-    if (lx >= lnx[n - 1]) return exp(lny[n - 1]);
-    int lo = 0, hi = n - 1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (lnx[mid] <= lx) lo = mid; else hi = mid;
-    }
-    const double f = (lx - lnx[lo]) / (lnx[lo + 1] - lnx[lo]);
-    return exp(lny[lo] + f * (lny[lo + 1] - lny[lo]));
 }
 
 struct Cell3 { int i, j, k; };

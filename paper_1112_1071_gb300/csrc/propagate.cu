@@ -74,6 +74,30 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
             continue;
         }
         for (;;) {
+            // modified random walk (Sect. 2.2) while the packet sits deep in a thick cell: each step
+            // one interaction against the cap and an isotropic re-emission at its end
+            bool killed = false;
+            while (a.mrw_gamma > 0.f) {
+                const float R0 = mrw_sphere<G>(g, a, pk.r);
+                if (R0 < 0.f) break;
+                if (++pk.nint > a.max_interactions) {
+                    killed = true;
+                    break;
+                }
+                lc.v[C_MRW]++;
+                const float v = mrw_take(d, o, a, pk, R0);
+                atomicAdd(t.acc + pk.r.ci, widen(v));
+                if (t.visits && pk.r.ci != pk.run_ci) {
+                    atomicAdd(t.visits + pk.r.ci, 1u);
+                    pk.run_ci = pk.r.ci;
+                }
+                if (a.peel && !a.rt)
+                    peel_event<G>(g, d, o, a, t, st.sed, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
+            }
+            if (killed) {
+                lc.v[C_KILLED]++;
+                break;
+            }
             const float tau = -logf(pk.rng.next());
             const int ev = walk_plain<G>(g, a, t, pk, tau, lc);
             if (ev == EV_ESCAPE) {

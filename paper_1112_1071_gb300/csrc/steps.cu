@@ -48,6 +48,23 @@ __global__ void k_step_tau(DevGrid g, DevDust dd, int64_t n, const float* pos, c
     }
 }
 
+template <int G>
+__global__ void k_step_wall_distance(DevGrid g, int64_t n, const float* pos, const int32_t* cell, float* dist,
+                                     float inv_L0, float L0) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        Ray r;
+        r.p = make_float3(pos[3 * q] * inv_L0, pos[3 * q + 1] * inv_L0, pos[3 * q + 2] * inv_L0);
+        r.i = cell[3 * q]; r.j = cell[3 * q + 1]; r.k = cell[3 * q + 2];
+        r.ci = lin(g, r.i, r.j, r.k);
+        dist[q] = wall_distance<G>(g, r) * L0;
+    }
+}
+
+__global__ void k_step_mrw_path(int64_t n, const float* tau0, const float* zeta, float* out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = mrw_path(tau0[q], zeta[q]);
+}
+
 __global__ void k_step_hg(float gg, int64_t n, const float* din, const float* u1, const float* u2, float* dout) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const float3 u = make_float3(din[3 * q], din[3 * q + 1], din[3 * q + 2]);
@@ -91,6 +108,23 @@ cudaError_t launch_step_tau(const DevGrid& g, const DevDust& d, int64_t n, const
     else if (g.type == GRID_CYLINDRICAL)
         k_step_tau<GRID_CYLINDRICAL><<<blocks_for(n), 256, 0, s>>>(g, d, n, pos, dir, nu, tau, inv_L0);
     else k_step_tau<GRID_SPHERICAL><<<blocks_for(n), 256, 0, s>>>(g, d, n, pos, dir, nu, tau, inv_L0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_wall_distance(const DevGrid& g, int64_t n, const float* pos, const int32_t* cell, float* dist,
+                                     float inv_L0, float L0, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (g.type == GRID_CARTESIAN)
+        k_step_wall_distance<GRID_CARTESIAN><<<blocks_for(n), 256, 0, s>>>(g, n, pos, cell, dist, inv_L0, L0);
+    else if (g.type == GRID_CYLINDRICAL)
+        k_step_wall_distance<GRID_CYLINDRICAL><<<blocks_for(n), 256, 0, s>>>(g, n, pos, cell, dist, inv_L0, L0);
+    else k_step_wall_distance<GRID_SPHERICAL><<<blocks_for(n), 256, 0, s>>>(g, n, pos, cell, dist, inv_L0, L0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_mrw_path(int64_t n, const float* tau0, const float* zeta, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_step_mrw_path<<<blocks_for(n), 256, 0, s>>>(n, tau0, zeta, out);
     return cudaGetLastError();
 }
 

@@ -8,19 +8,9 @@
 #include <math_constants.h>
 
 #include "hrt_internal.h"
+#include "planck.cuh"
 
 namespace hrt {
-
-// cgs, CODATA 2018 exact SI values
-constexpr double H_PLANCK = 6.62607015e-27;
-constexpr double K_BOLTZ = 1.380649e-16;
-constexpr double C_LIGHT = 2.99792458e10;
-
-__device__ __forceinline__ double planck_bnu(double nu, double T) {
-    const double x = H_PLANCK * nu / (K_BOLTZ * T);
-    if (x > 700.0) return 0.0;
-    return 2.0 * H_PLANCK * nu * nu * nu / (C_LIGHT * C_LIGHT) / expm1(x);
-}
 
 // one thread per temperature node
 __global__ void k_emission_tables(int nnu, const double* __restrict__ nu, const double* __restrict__ kappa, int nT,

@@ -27,6 +27,21 @@ __device__ __forceinline__ double invert_E(double A, const double* __restrict__ 
     return exp(lnT[lo] + f * (lnT[lo + 1] - lnT[lo]));
 }
 
+// y(x) linear in log-log on the table (lnx nodes ascending), clamped to the end values.
+__device__ __forceinline__ double loglog(double x, const double* __restrict__ lnx, const double* __restrict__ lny,
+                                         int n) {
+    const double lx = log(x);
+    if (!(lx > lnx[0])) return exp(lny[0]);
+    if (lx >= lnx[n - 1]) return exp(lny[n - 1]);
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lnx[mid] <= lx) lo = mid; else hi = mid;
+    }
+    const double f = (lx - lnx[lo]) / (lnx[lo + 1] - lnx[lo]);
+    return exp(lny[lo] + f * (lny[lo + 1] - lny[lo]));
+}
+
 // Table row for re-emission: nearest temperature node in log T, ties to the lower node.
 __device__ __forceinline__ int32_t nearest_row(double T, const double* __restrict__ lnT, int nT) {
     const double x = log(T);

@@ -38,7 +38,7 @@ class hrt_run_params(C.Structure):
         ("q_thres", C.c_double), ("delta_thres", C.c_double), ("kernel", C.c_int32),
         ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("regroup_threshold", C.c_int32),
         ("watchdog_ms", C.c_double), ("first_packet", C.c_int64), ("n_total", C.c_int64),
-        ("pda_min_visits", C.c_int64), ("raytrace_rays", C.c_int64),
+        ("pda_min_visits", C.c_int64), ("raytrace_rays", C.c_int64), ("mrw_gamma", C.c_double),
     ]
 
 
@@ -51,7 +51,7 @@ class hrt_iter_stats(C.Structure):
         ("n_peel_crossings", C.c_int64), ("n_killed", C.c_int64), ("clamp_low", C.c_int64),
         ("clamp_high", C.c_int64), ("ms_propagate", C.c_double), ("ms_total", C.c_double),
         ("kernel_launches", C.c_int64), ("n_pda", C.c_int64), ("pda_iterations", C.c_int64),
-        ("pda_residual", C.c_double),
+        ("pda_residual", C.c_double), ("n_mrw", C.c_int64),
     ]
 
     def as_dict(self):
@@ -101,6 +101,8 @@ _SIGS = {
     "hrt_step_philox": (C.c_int, [_i64, _vp, _vp, _vp, _vp]),
     "hrt_step_cell_exit": (C.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "hrt_step_tau_to_edge": (C.c_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "hrt_step_wall_distance": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
+    "hrt_step_mrw_path": (C.c_int, [_i64, _vp, _vp, _vp, _vp]),
     "hrt_step_hg_scatter": (C.c_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "hrt_step_sample_emission": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
     "hrt_step_sample_source": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
