@@ -192,43 +192,36 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         } while (mode == M_PEEL_DONE);
     };
 
-    // modified random walk (Sect. 2.2): steps while the packet sits deep in a thick cell, each one
-    // interaction against the cap and an isotropic re-emission at its end (peeled off like one);
-    // then a new flight
+    // modified random walk (Sect. 2.2) at the start of a flight: one step per event phase while the
+    // packet sits deep in a thick cell (each one interaction against the cap and an isotropic
+    // re-emission at its end, peeled off like one; the lane stays in M_MRW for the next phase, so a
+    // long chain never holds up its warp), else a new optical depth and the walk
     auto mrw_steps = [&]() {
-        // modified random walk (Sect. 2.2): steps while the packet sits deep in a thick cell,
-        // each one interaction against the cap and an isotropic re-emission at its end (peeled
-        // off like one); then a new flight
-        for (;;) {
-            const float R0 = mrw_sphere<G>(g, a, pk.r);
-            if (R0 < 0.f) {
-                tau = -logf(pk.rng.next());
-                ray_steps = 0;
-                zero_run = 0;
-                mode = M_WALK;
-                break;
-            }
-            if (++pk.nint > a.max_interactions) {
-                lc.v[C_KILLED]++;
-                end_packet();
-                break;
-            }
-            lc.v[C_MRW]++;
-            const float v = mrw_take(d, o, a, pk, R0);
-            if (pk.r.ci == dep_ci) {
-                dep_val += v;
-            } else {
-                flush_run(t, dep_ci, dep_val);
-                dep_ci = pk.r.ci;
-                dep_val = v;
-            }
-            porg = pk.r.p;
-            if constexpr (PEEL) {
-                if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !a.rt) {
-                    after_event(PEEL_ISO, 0, true);
-                    break;
-                }
-            }
+        const float R0 = mrw_sphere<G>(g, a, pk.r);
+        if (R0 < 0.f) {
+            tau = -logf(pk.rng.next());
+            ray_steps = 0;
+            zero_run = 0;
+            mode = M_WALK;
+            return;
+        }
+        if (++pk.nint > a.max_interactions) {
+            lc.v[C_KILLED]++;
+            end_packet();
+            return;
+        }
+        lc.v[C_MRW]++;
+        const float v = mrw_take(d, o, a, pk, R0);
+        if (pk.r.ci == dep_ci) {
+            dep_val += v;
+        } else {
+            flush_run(t, dep_ci, dep_val);
+            dep_ci = pk.r.ci;
+            dep_val = v;
+        }
+        porg = pk.r.p;
+        if constexpr (PEEL) {
+            if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !a.rt) after_event(PEEL_ISO, 0, true);
         }
     };
 

@@ -74,7 +74,7 @@ __device__ __forceinline__ float mrw_path(float tau0, float zeta) {
     if (zeta <= 0.69f) {
         const float lz = logf(zeta);
         x = logf(2.f / zeta);                    // the first term alone
-        for (int it = 0; it < 4; ++it) {
+        for (int it = 0; it < 2; ++it) {      // quadratic convergence from within e^-3x: 2 suffice in FP32
             const float q = expf(-x), q2 = q * q, q3 = q2 * q, q8 = q2 * q2 * q2 * q2;
             const float q15 = q8 * q3 * q3 * q;
             const float S = q * (1.f - q3 + q8 - q15);                // P / 2
@@ -85,7 +85,7 @@ __device__ __forceinline__ float mrw_path(float tau0, float zeta) {
         const float l1 = logf(1.f - zeta);
         const float c0 = logf(2.f * sqrtf(CUDART_PI_F));
         float w = fmaxf((c0 - l1) / (0.25f * PI2), 1.f);
-        for (int it = 0; it < 5; ++it) {
+        for (int it = 0; it < 3; ++it) {
             const float e = expf(-2.f * PI2 * w);
             const float f = c0 + 0.5f * logf(w) - 0.25f * PI2 * w + log1pf(e) - l1;
             const float df = 0.5f / w - 0.25f * PI2 - 2.f * PI2 * e / (1.f + e);

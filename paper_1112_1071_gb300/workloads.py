@@ -377,6 +377,26 @@ def cylindrical_disk(n_R: int = 120, n_z: int = 96, n_phi: int = 1, r_in_au: flo
                     obs_incl=np.arccos(cosi), obs_az=np.zeros(10), n_packets=n_packets, seed=seed)
 
 
+def embedded_envelope(n_r: int = 60, n_theta: int = 8, tau_550: float = 1e5, r_in_au: float = 1.0,
+                      r_out_au: float = 1000.0, power: float = 1.5, n_packets: int = 100_000,
+                      seed: int = 14) -> Workload:
+    """A star embedded in an optically thick envelope, rho ∝ r^-power (an infalling envelope),
+    on a spherical-polar grid (r log-spaced r_in to r_out, n_theta uniform cones, one phi cell)
+    with an empty inner cavity, normalised to a radial tau_550 at cell centres: the regime where
+    packets re-emitted deep inside need the modified random walk (Sect. 2.2)."""
+    rw = r_in_au * AU * (r_out_au / r_in_au) ** (np.arange(n_r + 1) / n_r)
+    walls = [rw, np.linspace(0.0, math.pi, n_theta + 1), np.array([0.0, 2.0 * math.pi])]
+    rc = 0.5 * (rw[1:] + rw[:-1])
+    rho0 = tau_550 / (chi_at_lambda_um(0.55) * np.sum((rc / AU) ** -power * np.diff(rw)))
+    rho = np.broadcast_to(rho0 * (rc / AU) ** -power, (1, n_theta, n_r)).astype(np.float32).copy()
+    nu, chi, alb, g = dust_table()
+    cosi = 0.05 + 0.1 * np.arange(10)
+    return Workload(name="embedded_envelope", grid_type="spherical", walls=walls, rho=rho, nu=nu, chi=chi,
+                    albedo=alb, g=g, T_nodes=temperature_nodes(),
+                    sources=[dict(pos=(0.0, 0.0, 0.0), L=LSUN, Teff=5800.0)], obs_incl=np.arccos(cosi),
+                    obs_az=np.zeros(10), n_packets=n_packets, seed=seed)
+
+
 WORKLOADS = {
     "tiny_sphere": tiny_sphere,
     "flared_disk": flared_disk,
