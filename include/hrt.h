@@ -329,9 +329,14 @@ int hrt_net_temperature_target(hrt_ctx* ctx, float* d_out, int64_t n);
 int hrt_net_warm_start(hrt_net* net, hrt_ctx* ctx);
 /* Single-layer hooks on FP32 device tensors (converted to BF16 inside): 'same' 3x3x3 conv with
  * bias and optional ReLU (Cin % 16 == 0, Cout % 32 == 0), and its input, weight and bias
- * gradients for an output gradient dy (Cin, Cout % 32 == 0).  Weights [27][Cin][Cout]. */
+ * gradients for an output gradient dy (Cin, Cout % 32 == 0).  Weights [27][Cin][Cout].  The
+ * convolutions run on the tcgen05 tensor cores (accumulator in tensor memory); HRT_ETIMEDOUT if
+ * one of their bounded waits gave up.  hrt_nn_conv3d_mma is the same forward convolution with
+ * warp-level mma.sync, the baseline the tcgen05 kernel is measured against. */
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
                   int relu, float* d_y, void* stream);
+int hrt_nn_conv3d_mma(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                      const float* d_b, int relu, float* d_y, void* stream);
 int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
                            const float* d_dy, float* d_dx, float* d_dw, float* d_db, void* stream);
 

@@ -1,5 +1,7 @@
 // Kernels of the learned warm start: a 3-D convolutional encoder-decoder on channels-last BF16
-// tensors with FP32 accumulation on the tensor cores (mma.sync m16n8k16 BF16).
+// tensors with FP32 accumulation.  The convolution the network runs is the tcgen05 kernel of
+// nn_tc.cu; this file keeps the warp-level mma.sync (m16n8k16 BF16) formulation of the same
+// convolution as the measured baseline (conv3d_mma) and the weight gradient.
 //
 // conv3d (3x3x3, zero padding one voxel) as an implicit GEMM: out[v][n] = b[n] +
 //   sum_{tap, k} in[v + off(tap)][k] * B[tap][n][k].  Forward: B = W^T stored [27][Cout][Cin].
@@ -175,8 +177,8 @@ __global__ void __launch_bounds__(128) k_conv3d(const bf16* __restrict__ in, con
     }
 }
 
-cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
-                   int Cout, bool flip, bool relu, cudaStream_t s) {
+cudaError_t conv3d_mma(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
+                       int Cout, bool flip, bool relu, cudaStream_t s) {
     if (Cin % 16 != 0 || Cout % 32 != 0) return cudaErrorInvalidValue;
     const long long V = (long long)D * H * W;
     const dim3 grid((unsigned)((V + 63) / 64), (unsigned)((Cout + 63) / 64), (unsigned)N);

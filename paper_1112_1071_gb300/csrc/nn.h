@@ -12,8 +12,14 @@ using bf16 = __nv_bfloat16;
 
 // 'same' 3x3x3 convolution: out = act(bias + conv(in, B)); Cin % 16 == 0, Cout % 32 == 0.
 // Forward: B = W^T; data gradient: in = dY, B = W, flip = true, no bias, no ReLU.
+// conv3d runs on the tcgen05 tensor cores (nn_tc.cu); conv3d_mma is the same convolution with
+// warp-level mma.sync, kept as the measured baseline.
 cudaError_t conv3d(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
                    int Cout, bool flip, bool relu, cudaStream_t s);
+cudaError_t conv3d_mma(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W,
+                       int Cin, int Cout, bool flip, bool relu, cudaStream_t s);
+// after a synchronisation of s: *failed = 1 if a tcgen05 convolution block gave up a wait
+cudaError_t tc_status(int* failed, cudaStream_t s);
 // dw [27][Cin][Cout] += sum over voxels (FP32 atomics; zero dw first)
 cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
                          cudaStream_t s);

@@ -532,8 +532,21 @@ int hrt_net_warm_start(hrt_net* n, hrt_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------- single-layer hooks
+static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                       const float* d_b, int relu, float* d_y, void* stream, bool legacy);
+
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
                   int relu, float* d_y, void* stream) {
+    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, false);
+}
+
+int hrt_nn_conv3d_mma(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                      const float* d_b, int relu, float* d_y, void* stream) {
+    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, true);
+}
+
+static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                       const float* d_b, int relu, float* d_y, void* stream, bool legacy) {
     if (N < 1 || D < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32 || !d_x || !d_w || !d_y) return HRT_EINVAL;
     const cudaStream_t s = (cudaStream_t)stream;
     const long long NV = (long long)N * D * H * W;
@@ -544,11 +557,15 @@ int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_
     bf16* wt = dalloc<bf16>(27LL * Cin * Cout, e);
     if (e == cudaSuccess) e = nn::f32_to_bf16(d_x, x, NV * Cin, s);
     if (e == cudaSuccess) e = nn::weights_bf16(d_w, wb, wt, Cin, Cin, Cout, s);
-    if (e == cudaSuccess) e = nn::conv3d(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
+    if (e == cudaSuccess)
+        e = legacy ? nn::conv3d_mma(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
+                   : nn::conv3d(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
     if (e == cudaSuccess) e = nn::bf16_to_f32(y, d_y, NV * Cout, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int failed = 0;
+    if (e == cudaSuccess) e = nn::tc_status(&failed, s);
     cudaFree(x); cudaFree(y); cudaFree(wb); cudaFree(wt);
     if (e != cudaSuccess) cudaGetLastError();
+    if (e == cudaSuccess && failed) return HRT_ETIMEDOUT;
     return e == cudaSuccess ? HRT_OK : HRT_ECUDA;
 }
 
@@ -573,9 +590,11 @@ int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const 
     if (e == cudaSuccess) e = nn::bias_grad(g, d_db, NV, Cout, s);
     if (e == cudaSuccess) e = nn::conv3d(g, wb, nullptr, gx, N, D, H, W, Cout, Cin, true, false, s);
     if (e == cudaSuccess) e = nn::bf16_to_f32(gx, d_dx, NV * Cin, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int failed = 0;
+    if (e == cudaSuccess) e = nn::tc_status(&failed, s);
     cudaFree(x); cudaFree(g); cudaFree(gx); cudaFree(wb); cudaFree(wt);
     if (e != cudaSuccess) cudaGetLastError();
+    if (e == cudaSuccess && failed) return HRT_ETIMEDOUT;
     return e == cudaSuccess ? HRT_OK : HRT_ECUDA;
 }
 

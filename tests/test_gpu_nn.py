@@ -29,7 +29,7 @@ def close(got, want, rel):
     assert np.all(err <= rel * np.abs(want) + rel * scale), (err.max(), scale)
 
 
-@pytest.mark.parametrize("cin,cout,relu", [(32, 64, 1), (16, 32, 0), (64, 32, 1)])
+@pytest.mark.parametrize("cin,cout,relu", [(32, 64, 1), (16, 32, 0), (64, 32, 1), (64, 128, 1), (48, 96, 0)])
 def test_conv3d_forward_matches_oracle(cin, cout, relu):
     torch = torch_cuda()
     rng = np.random.default_rng(cin + cout)
@@ -169,3 +169,23 @@ def test_warm_start_writes_the_network_prediction():
     st = m.run_iteration()
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
     L.hrt_net_destroy(net)
+
+
+def test_tcgen05_conv_equals_the_mma_sync_baseline():
+    """The tensor-memory kernel and the warp-level mma.sync kernel accumulate the same BF16
+    products in FP32; after the BF16 store they agree to one BF16 ulp (summation order)."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(3)
+    L = hrt.load()
+    for n, d, h, w, cin, cout in [(1, 9, 10, 11, 32, 32), (2, 5, 6, 7, 64, 64)]:
+        x = dev(rng.normal(size=(n, d, h, w, cin)).astype(np.float32))
+        wt = dev((rng.normal(size=(3, 3, 3, cin, cout)) / np.sqrt(27 * cin)).astype(np.float32))
+        b = dev(rng.normal(size=cout).astype(np.float32))
+        y1 = torch.empty((n, d, h, w, cout), dtype=torch.float32, device="cuda")
+        y2 = torch.empty_like(y1)
+        assert L.hrt_nn_conv3d(n, d, h, w, cin, cout, x.data_ptr(), wt.data_ptr(), b.data_ptr(), 1, y1.data_ptr(), None) == 0
+        assert L.hrt_nn_conv3d_mma(n, d, h, w, cin, cout, x.data_ptr(), wt.data_ptr(), b.data_ptr(), 1, y2.data_ptr(),
+                                   None) == 0
+        a, c = y1.cpu().numpy(), y2.cpu().numpy()
+        assert np.all(np.abs(a - c) <= 2.0 ** -7 * np.abs(c) + 1e-6)
+
