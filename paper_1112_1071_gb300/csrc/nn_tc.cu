@@ -2,17 +2,20 @@
 // implicit GEMM out[v][n] = act(b[n] + sum_{tap, k} in[v + off(tap)][k] * B[tap][n][k]) with the
 // FP32 accumulator in tensor memory.
 //
-// Per block (128 threads): a tile of 128 voxels (the MMA's M) x BN outputs (its N).  The K loop
-// runs over (tap, KC-channel chunk) stages: every thread gathers its voxel's KC channels at the
-// tap offset (zero outside the grid) and a share of the B rows into shared memory with
-// cp.async, in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
-// 128 bytes apart along K, KC * 16 bytes apart per 8 rows); one thread issues KC / 16
-// tcgen05.mma (M = 128, N = BN, K = 16, BF16 in, FP32 accumulate) and commits them to the
-// stage's mbarrier.  Two stage buffers: the gather of stage s + 1 overlaps the MMAs of stage s,
-// and a buffer is refilled only after the mbarrier shows its MMAs complete.  The epilogue reads
-// each voxel's row of the accumulator (tensor-memory lane = voxel) with tcgen05.ld, adds the
-// bias, applies ReLU and stores BF16.  Every wait is bounded (2 s): past it the block records
-// an error, frees its tensor memory and returns.
+// Per block (128 threads): a brick of 16 (y) x 8 (x) voxels of one z plane is the MMA's M = 128
+// (row = 8 y + x = tensor-memory lane), BN outputs its N.  For each chunk of 16 input channels
+// the block loads a halo of 3 (z) x 18 (y) x 10 (x) voxels, as three x-shifted copies laid out in
+// the no-swizzle K-major core-matrix layout (8 voxels along x x 16 bytes of channels per core
+// matrix, the chunk's two core matrices 128 bytes apart, one 8-voxel group per (copy, z, y) 256
+// bytes apart), and the weights of TG taps (all 27, or 9 when BN = 128) in the same layout.  The
+// A operand of tap (dz, dy, dx) is 16 consecutive groups of the dx copy starting at (dz, dy): a
+// shared-memory descriptor, no copy per tap; the input is read from L2 about 4 times instead of
+// 27.  After one cp.async wait and one barrier a single thread issues the TG tcgen05.mma of the
+// phase back to back (M = 128, N = BN, K = 16, BF16 in, FP32 accumulate) and commits them to an
+// mbarrier, which every thread waits on before the next phase overwrites the operands; other
+// resident blocks overlap their loads with these MMAs.  The epilogue reads each voxel's row of
+// the accumulator with tcgen05.ld, adds the bias, applies ReLU and stores BF16.  Every wait is
+// bounded (2 s): past it the block records an error, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -37,33 +40,42 @@ __device__ __forceinline__ void cp_async16_zfill(uint32_t smem, const void* gmem
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem), "l"(gmem), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// byte offset of (row, 16-byte chunk along K) in a KC-wide no-swizzle K-major tile
-template <int KC>
-__device__ __forceinline__ uint32_t core_off(int row, int chunk) {
-    return (uint32_t)((row >> 3) * (KC * 16) + chunk * 128 + (row & 7) * 16);
-}
+constexpr int BRICK_Y = 16, BRICK_X = 8, HALO_Y = BRICK_Y + 2;
+constexpr int KC = 16;                              // input channels per halo
+constexpr int GROUP = KC * 16;                      // one 8-voxel group: two core matrices
+constexpr int HALO_GROUPS = 3 * 3 * HALO_Y;         // (dx copy, z, y)
+constexpr int HALO_BYTES = HALO_GROUPS * GROUP;
+
+// taps per phase: all 27 while their weights take at most 32 KB, else 9 (one z plane of taps)
+template <int BN>
+constexpr int taps_per_phase() { return 27 * BN * KC * 2 <= 32768 ? 27 : 9; }
+template <int BN>
+constexpr int smem_bytes() { return HALO_BYTES + taps_per_phase<BN>() * BN * KC * 2 + 16; }
 
 }  // namespace
 
-template <int KC, int BN>
+template <int BN>
 __global__ void __launch_bounds__(128) k_conv3d_tc(const bf16* __restrict__ in, const bf16* __restrict__ B,
                                                    const float* __restrict__ bias, bf16* __restrict__ out, int D, int H,
                                                    int W, int Cin, int Cout, int flip, int relu) {
-    constexpr int BM = 128;
-    constexpr int A_BYTES = BM * KC * 2, B_BYTES = BN * KC * 2;
     constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
-    constexpr int CH = KC / 8;                      // 16-byte chunks per row and stage
+    constexpr int TG = taps_per_phase<BN>();
+    constexpr int B_TILE = BN * KC * 2;             // one tap's weights
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t sA = tc::smem_addr(smem);
-    const uint32_t sB = sA + 2 * A_BYTES;
-    const uint32_t bar0 = sB + 2 * B_BYTES;         // two 8-byte mbarriers
-    const uint32_t slot = bar0 + 16;                // tensor-memory address written by the allocation
+    const uint32_t sH = tc::smem_addr(smem);
+    const uint32_t sB = sH + HALO_BYTES;
+    const uint32_t bar = sB + TG * B_TILE;          // one 8-byte mbarrier
+    const uint32_t slot = bar + 8;                  // tensor-memory address written by the allocation
     const int tid = threadIdx.x, warp = tid >> 5;
-    const long long V = (long long)D * H * W;
-    const long long v0 = (long long)blockIdx.x * BM;
+    const int nbx = (W + BRICK_X - 1) / BRICK_X, nby = (H + BRICK_Y - 1) / BRICK_Y;
+    const int x0 = (blockIdx.x % nbx) * BRICK_X;
+    const int y0 = ((blockIdx.x / nbx) % nby) * BRICK_Y;
+    const int z0 = blockIdx.x / (nbx * nby);
     const int n0 = blockIdx.y * BN;
+    const long long V = (long long)D * H * W;
     const bf16* inb = in + (long long)blockIdx.z * V * Cin;
     bf16* outb = out + (long long)blockIdx.z * V * Cout;
 
@@ -72,8 +84,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const bf16* __restrict__ in, 
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(bar0, 1);
-        tc::mbar_init(bar0 + 8, 1);
+        tc::mbar_init(bar, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
@@ -82,43 +93,44 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const bf16* __restrict__ in, 
     uint32_t tmem;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot) : "memory");
 
-    // this thread's voxel (row tid of the tile) and its grid position
-    const long long v = v0 + tid;
-    const bool vin = v < V;
-    int x = 0, y = 0, z = 0;
-    if (vin) {
-        x = (int)(v % W);
-        y = (int)((v / W) % H);
-        z = (int)(v / ((long long)W * H));
-    }
-    const int kchunks = Cin / KC;
-    const int S = 27 * kchunks;
-
-    auto load = [&](int s, int buf) {
-        const int tap = s / kchunks, k0 = (s % kchunks) * KC;
-        const int btap = flip ? 26 - tap : tap;
-        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-        const bool ok = vin && zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
-        const bf16* src = ok ? inb + (((long long)zz * H + yy) * W + xx) * Cin + k0 : inb;
-        const uint32_t a = sA + buf * A_BYTES;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) cp_async16_zfill(a + core_off<KC>(tid, c), ok ? (const void*)(src + c * 8) : src, ok);
-        const uint32_t b = sB + buf * B_BYTES;
-        for (int q = tid; q < BN * CH; q += 128) {
-            const int n = q / CH, c = q % CH;
-            const bool okb = n0 + n < Cout;
-            const bf16* bs = okb ? B + ((long long)btap * Cout + n0 + n) * Cin + k0 + c * 8 : B;
-            cp_async16_zfill(b + core_off<KC>(n, c), bs, okb);
+    // halo of channels k0 .. k0 + 15: thread -> (group parity, voxel xr, 16-byte chunk c); each
+    // pass covers 8 groups, 21 passes the 162 groups (the last partly)
+    auto load_halo = [&](int k0) {
+        const int c = tid & 1, xr = (tid >> 1) & 7, gsub = tid >> 4;
+        for (int g = gsub; g < HALO_GROUPS; g += 8) {
+            const int hy = g % HALO_Y, hz = (g / HALO_Y) % 3, dxc = g / (3 * HALO_Y);
+            const int xx = x0 + xr + dxc - 1, yy = y0 + hy - 1, zz = z0 + hz - 1;
+            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H && zz >= 0 && zz < D;
+            const bf16* src = ok ? inb + (((long long)zz * H + yy) * W + xx) * Cin + k0 + c * 8 : inb;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sH + g * GROUP + c * 128 + xr * 16),
+                         "l"(src), "r"(ok ? 16 : 0)
+                         : "memory");
         }
-        cp_async_commit();
+    };
+    // weights of taps t0 .. t0 + TG - 1 for channels k0 .. k0 + 15: tile (tap) -> rows n -> 2 chunks
+    auto load_b = [&](int t0, int k0) {
+        for (int q = tid; q < TG * BN * 2; q += 128) {
+            const int c = q & 1, n = (q >> 1) % BN, t = q / (2 * BN);
+            const int btap = flip ? 26 - (t0 + t) : t0 + t;
+            const bf16* bs = B + ((long long)btap * Cout + n0 + n) * Cin + k0 + c * 8;
+            cp_async16_zfill(sB + t * B_TILE + (n >> 3) * GROUP + c * 128 + (n & 7) * 16, bs, true);
+        }
     };
 
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(BM, BN);
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, BN);
+    const int kchunks = Cin / KC;
+    const int phases = kchunks * (27 / TG);
     bool failed = false;
-    load(0, 0);
-    for (int s = 0; s < S; ++s) {
-        const int buf = s & 1;
-        cp_async_wait_all();
+    for (int ph = 0; ph < phases && !failed; ++ph) {
+        const int ci = ph / (27 / TG), t0 = (ph % (27 / TG)) * TG;
+        // the operands of the previous phase are free once its MMAs are complete
+        if (ph > 0 && !tc::mbar_wait(bar, (uint32_t)(ph - 1) & 1u, WAIT_LIMIT_NS)) failed = true;
+        if (!failed) {
+            if (t0 == 0) load_halo(ci * KC);
+            load_b(t0, ci * KC);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
         tc::fence_proxy_async_smem();
         if (__syncthreads_or(failed ? 1 : 0)) {
             failed = true;
@@ -126,26 +138,24 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const bf16* __restrict__ in, 
         }
         if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a = sA + buf * A_BYTES, b = sB + buf * B_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < KC / 16; ++kk)
-                tc::mma_bf16(tmem, tc::smem_desc(a + kk * 256, 128, KC * 16), tc::smem_desc(b + kk * 256, 128, KC * 16),
-                             IDESC, (s > 0 || kk > 0) ? 1u : 0u);
-            tc::mma_commit(bar0 + 8 * buf);
-        }
-        if (s + 1 < S) {
-            // the other buffer is free once the MMAs of stage s - 1 are complete
-            if (s >= 1 && !tc::mbar_wait(bar0 + 8 * (buf ^ 1), (uint32_t)((s - 1) >> 1) & 1u, WAIT_LIMIT_NS)) failed = true;
-            if (!failed) load(s + 1, buf ^ 1);
+#pragma unroll 1
+            for (int t = 0; t < TG; ++t) {
+                const int tap = t0 + t;
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;          // 0..2 = offset + 1
+                const uint32_t a = sH + ((dx * 3 + dz) * HALO_Y + dy) * GROUP;
+                tc::mma_bf16(tmem, tc::smem_desc(a, 128, GROUP), tc::smem_desc(sB + t * B_TILE, 128, GROUP), IDESC,
+                             (ph > 0 || t > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(bar);
         }
     }
-    if (!failed) {
-        const int last = S - 1;
-        if (!tc::mbar_wait(bar0 + 8 * (last & 1), (uint32_t)(last >> 1) & 1u, WAIT_LIMIT_NS)) failed = true;
-    }
+    if (!failed && !tc::mbar_wait(bar, (uint32_t)(phases - 1) & 1u, WAIT_LIMIT_NS)) failed = true;
     failed = __syncthreads_or(failed ? 1 : 0) != 0;
     if (!failed) {
         tc::fence_after_sync();
+        const int yy = y0 + tid / BRICK_X, xx = x0 + tid % BRICK_X;
+        const bool vin = yy < H && xx < W;
+        const long long v = ((long long)z0 * H + yy) * W + xx;
         const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -177,22 +187,22 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const bf16* __restrict__ in, 
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
 }
 
-// Dynamic shared memory per block: the two stage buffers, padded when needed so that no more
-// blocks are resident on an SM than its 512 tensor-memory columns serve (an allocation then never
+// Dynamic shared memory per block: halo and weights, padded when needed so that no more blocks
+// are resident on an SM than its 512 tensor-memory columns serve (an allocation then never
 // waits for another block).
-template <int KC, int BN>
+template <int BN>
 static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W,
                              int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     constexpr int NCOLS = BN < 32 ? 32 : BN;
     constexpr int MAX_RESIDENT = 512 / NCOLS;
     static int smem = 0;
     if (smem == 0) {
-        int bytes = 2 * 128 * KC * 2 + 2 * BN * KC * 2 + 32;
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<KC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        int bytes = smem_bytes<BN>();
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         for (;;) {
             int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_tc<KC, BN>, 128, bytes);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_tc<BN>, 128, bytes);
             if (e != cudaSuccess) return e;
             if (per_sm <= MAX_RESIDENT) break;
             bytes += 4096;
@@ -200,26 +210,18 @@ static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, 
         }
         smem = bytes;
     }
-    const long long V = (long long)D * H * W;
-    const dim3 grid((unsigned)((V + 127) / 128), (unsigned)(Cout / BN), (unsigned)N);
-    k_conv3d_tc<KC, BN><<<grid, 128, smem, s>>>(in, Bw, bias, out, D, H, W, Cin, Cout, flip, relu);
+    const unsigned bricks = (unsigned)(((W + BRICK_X - 1) / BRICK_X) * ((H + BRICK_Y - 1) / BRICK_Y) * D);
+    const dim3 grid(bricks, (unsigned)(Cout / BN), (unsigned)N);
+    k_conv3d_tc<BN><<<grid, 128, smem, s>>>(in, Bw, bias, out, D, H, W, Cin, Cout, flip, relu);
     return cudaGetLastError();
-}
-
-template <int KC>
-static cudaError_t dispatch_bn(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W,
-                               int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
-    if (Cout % 128 == 0) return launch_tc<KC, 128>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
-    if (Cout % 64 == 0) return launch_tc<KC, 64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
-    return launch_tc<KC, 32>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
 
 cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
                    int Cout, bool flip, bool relu, cudaStream_t s) {
     if (Cin % 16 != 0 || Cout % 32 != 0 || Cin <= 0 || Cout <= 0) return cudaErrorInvalidValue;
-    if (Cin % 64 == 0) return dispatch_bn<64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
-    if (Cin % 32 == 0) return dispatch_bn<32>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
-    return dispatch_bn<16>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    if (Cout % 128 == 0) return launch_tc<128>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    if (Cout % 64 == 0) return launch_tc<64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    return launch_tc<32>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
 
 cudaError_t tc_status(int* failed, cudaStream_t s) {
