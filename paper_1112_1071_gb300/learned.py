@@ -80,6 +80,33 @@ def generate(seeds, n, packets, iters, tau, torch, log=None):
     return torch.stack(X), torch.stack(Y), info
 
 
+def bench_conv(torch, log, reps=5):
+    """Device time per launch of the 'same' 3x3x3 convolution through its two C-ABI hooks
+    (tcgen05 with the accumulator in tensor memory, and the mma.sync baseline) on three shapes,
+    by CUDA events around reps calls each (the hooks' BF16 conversions included)."""
+    L = hrt.load()
+    out = []
+    for n, d, cin, cout in ((4, 64, 32, 32), (2, 64, 64, 64), (1, 32, 128, 128)):
+        x = torch.randn((n, d, d, d, cin), device="cuda")
+        w = torch.randn((3, 3, 3, cin, cout), device="cuda") * (27 * cin) ** -0.5
+        b = torch.zeros(cout, device="cuda")
+        y = torch.empty((n, d, d, d, cout), device="cuda")
+        row = dict(shape=f"{n}x{d}^3 {cin}->{cout}", gflop=2 * 27 * cin * cout * n * d ** 3 / 1e9)
+        for name, f in (("tcgen05", L.hrt_nn_conv3d), ("mma_sync", L.hrt_nn_conv3d_mma)):
+            for _ in range(2):
+                hrt.check(None, f(n, d, d, d, cin, cout, x.data_ptr(), w.data_ptr(), b.data_ptr(), 1, y.data_ptr(), None))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                hrt.check(None, f(n, d, d, d, cin, cout, x.data_ptr(), w.data_ptr(), b.data_ptr(), 1, y.data_ptr(), None))
+            e1.record()
+            torch.cuda.synchronize()
+            row[name + "_ms"] = e0.elapsed_time(e1) / reps
+        out.append(row)
+        log(json.dumps(row))
+    return out
+
+
 def train(net, X, Y, epochs, lr, batch, torch, log=None):
     L = hrt.load()
     M, n = X.shape[0], X.shape[1]
@@ -174,9 +201,14 @@ def main():
     ap.add_argument("--base", type=int, default=32)
     ap.add_argument("--levels", type=int, default=2)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--bench-conv", action="store_true",
+                    help="only time the 3x3x3 convolution (tcgen05 and mma.sync hooks) on three shapes")
     a = ap.parse_args()
     log = lambda s: print(s, flush=True)
     L = hrt.load()
+    if a.bench_conv:
+        bench_conv(torch, log)
+        return
     t0 = time.time()
     X, Y, info = generate(range(1000, 1000 + a.train), a.n, a.packets, a.iters, a.tau, torch, log)
     gen_s = time.time() - t0
