@@ -373,7 +373,7 @@ int prepare(hrt_ctx* ctx) {
     CK(ctx->d_state.alloc(4), "select state");
     CK(ctx->d_hist.alloc(256), "select histogram");
     CK(ctx->d_abort.alloc(1), "abort flag");
-    CK(ctx->d_work.alloc(2), "work counter");
+    CK(ctx->d_work.alloc(3), "work counter");
     CK(ctx->d_report.alloc(WD_REPORTS * WD_FIELDS), "watchdog report");
     CK(ctx->d_report_count.alloc(1), "watchdog report");
     if (!ctx->h_stats) CK(cudaMallocHost(&ctx->h_stats, sizeof(unsigned long long) * (N_COUNTERS + 8)), "pinned stats");
@@ -440,7 +440,8 @@ int hrt_destroy(hrt_ctx* ctx) {
     ctx->d_report.release(); ctx->d_report_count.release();
     ctx->d_uoff.release(); ctx->d_un.release(); ctx->d_img_bin.release(); ctx->d_row.release();
     ctx->d_keys.release(); ctx->d_esc.release(); ctx->d_counters.release(); ctx->d_state.release();
-    ctx->d_hist.release(); ctx->d_abort.release(); ctx->d_work.release();
+    ctx->d_hist.release(); ctx->d_abort.release(); ctx->d_work.release(); ctx->d_peel_q.release();
+    ctx->d_peel_hist.release(); ctx->d_peel_sums.release(); ctx->d_peel_order.release();
     if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
     for (auto e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -828,9 +829,25 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         job.src.col = ctx->d_src_col.p;
         launched++;
     }
+    if (A.peel && P.kernel != HRT_KERNEL_PLAIN && ctx->grid.n1 < 32768 && ctx->grid.n2 < 32768 && ctx->grid.n3 < 32768) {
+        // queue for the peel pass (16-bit cell indices per axis): two events per packet (an
+        // overflow is peeled inline), at most 2^27 events (6 GiB)
+        const int64_t cap = std::min<int64_t>(std::max<int64_t>(2 * n_packets, (int64_t)1 << 20), (int64_t)1 << 27);
+        if (ctx->d_peel_q.n < (size_t)cap) CK(ctx->d_peel_q.alloc((size_t)cap), "peel queue");
+        job.args.peel_q = ctx->d_peel_q.p;
+        job.args.peel_n = ctx->d_work.p + 2;
+        job.args.peel_cap = (int64_t)ctx->d_peel_q.n;
+    }
     cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
                                                  : launch_propagate_event(job, L, s, &launched);
     CK(e, "propagate");
+    if (job.args.peel_q) {
+        const size_t nk = (size_t)nc + 1;
+        if (ctx->d_peel_hist.n < nk) CK(ctx->d_peel_hist.alloc(nk), "peel sort");
+        if (ctx->d_peel_sums.n < nk / 1024 + 1) CK(ctx->d_peel_sums.alloc(nk / 1024 + 1), "peel sort");
+        if (ctx->d_peel_order.n < ctx->d_peel_q.n) CK(ctx->d_peel_order.alloc(ctx->d_peel_q.n), "peel sort");
+        CK(launch_peel_pass(job, ctx->d_peel_hist.p, ctx->d_peel_sums.p, ctx->d_peel_order.p, s, &launched), "peel pass");
+    }
     CK(cudaEventRecord(ctx->ev[1], s), "event");
     if (raytrace) {
         std::vector<int32_t> qd_off, qd_j, qd_bin, qs_off, qs_j, qs_bin;

@@ -114,7 +114,9 @@ struct hrt_ctx {
     DBuf<unsigned long long> d_keys, d_esc, d_counters, d_state;
     DBuf<unsigned int> d_hist;
     DBuf<int32_t> d_abort;
-    DBuf<unsigned long long> d_work;
+    DBuf<unsigned long long> d_work;            // [0] next packet, [1] launch stamp, [2] peel events queued
+    DBuf<uint32_t> d_peel_hist, d_peel_sums, d_peel_order;   // its counting sort by cell
+    DBuf<hrt::PeelEvent> d_peel_q;                  // peel-off events of an imaging pass (event kernel)
     DBuf<float> d_report;
     DBuf<unsigned> d_report_count;
     // ---- partial diffusion approximation (App. A)

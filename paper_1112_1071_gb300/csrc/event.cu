@@ -8,6 +8,8 @@
 //   * walk phase: all walking lanes (packet rays and peel rays share one step) take cell
 //     crossings together while at least `regroup` lanes are walking, so the walk -- where
 //     nearly all time goes -- runs in long converged loops.
+// In an imaging pass the peel rays that need a walk are queued instead (one record per event)
+// and walked afterwards by a separate pass, one ray per thread (peel.cu).
 // Lanes that need a packet draw consecutive packet ids with one atomic per warp.  Packet p
 // always draws from its own Philox stream, so the histories do not depend on which lane or
 // launch shape runs them.  Deposits are the FP32 products kappa * l (scaled length), merged
@@ -24,8 +26,6 @@ namespace hrt {
 
 enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE, M_MRW };
 
-// Optical depth beyond which a peel-off ray stops: exp(-40) = 4e-18 of its weight remains.
-constexpr float PEEL_TAU_STOP = 40.f;
 
 // Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
 // With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
@@ -121,6 +121,24 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     auto after_event = [&](int kind, int relocate, bool raytraced) {
         if constexpr (PEEL) {
             if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !(raytraced && a.rt)) {
+                // peel rays that need a walk go to the queue of the peel pass while it has room
+                if (a.peel_q && !(relocate && s.col)) {
+                    const unsigned long long slot = atomicAdd(a.peel_n, 1ull);
+                    if (slot < (unsigned long long)a.peel_cap) {
+                        PeelEvent e;
+                        e.px = porg.x; e.py = porg.y; e.pz = porg.z;
+                        e.ci = pk.r.ci;
+                        e.i = (int16_t)pk.r.i; e.j = (int16_t)pk.r.j; e.k = (int16_t)pk.r.k;
+                        e.flags = (int16_t)((relocate ? 1 : 0) | (kind == PEEL_HG ? 2 : 0));
+                        e.ux = uin.x; e.uy = uin.y; e.uz = uin.z;
+                        e.chi = pk.dust.chi;
+                        e.sbin = pk.sbin;
+                        e.pad = 0;
+                        a.peel_q[slot] = e;
+                        start_walk();
+                        return;
+                    }
+                }
                 saved = pk.r;
                 pkind = kind;
                 prelocate = relocate;
@@ -416,14 +434,17 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
     const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
+    cudaError_t e;
     if (job.grid.type == GRID_CARTESIAN)
-        return peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
-                    : launch_event_shape<GRID_CARTESIAN, false>(j, ll, bps, s);
-    if (job.grid.type == GRID_CYLINDRICAL)
-        return peel ? launch_event_shape<GRID_CYLINDRICAL, true>(j, ll, bps, s)
-                    : launch_event_shape<GRID_CYLINDRICAL, false>(j, ll, bps, s);
-    return peel ? launch_event_shape<GRID_SPHERICAL, true>(j, ll, bps, s)
-                : launch_event_shape<GRID_SPHERICAL, false>(j, ll, bps, s);
+        e = peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
+                 : launch_event_shape<GRID_CARTESIAN, false>(j, ll, bps, s);
+    else if (job.grid.type == GRID_CYLINDRICAL)
+        e = peel ? launch_event_shape<GRID_CYLINDRICAL, true>(j, ll, bps, s)
+                 : launch_event_shape<GRID_CYLINDRICAL, false>(j, ll, bps, s);
+    else
+        e = peel ? launch_event_shape<GRID_SPHERICAL, true>(j, ll, bps, s)
+                 : launch_event_shape<GRID_SPHERICAL, false>(j, ll, bps, s);
+    return e;
 }
 
 // ---------------------------------------------------------------- many models, one launch

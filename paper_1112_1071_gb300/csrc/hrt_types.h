@@ -119,6 +119,19 @@ enum Counter {
 
 constexpr int N_ESC_MU = 10;
 
+// A peel-off event queued by the propagation kernel of an imaging pass (Sect. 2.6.2): the peel
+// rays from it to every observer are walked by a separate pass, one ray per thread.
+struct PeelEvent {
+    float px, py, pz;              // event position (scaled)
+    int32_t ci;                    // its cell (linear; unused when relocating)
+    int16_t i, j, k;               // its cell per axis
+    int16_t flags;                 // bit 0: locate the cell along the observer direction; bit 1: HG
+    float ux, uy, uz;              // incoming direction (Henyey-Greenstein scattering)
+    float chi;                     // extinction at the packet frequency
+    int32_t sbin;                  // SED bin of the packet frequency
+    int32_t pad;
+};
+
 struct RunArgs {
     int64_t n_packets;
     int64_t first_packet;
@@ -134,6 +147,9 @@ struct RunArgs {
                                    // at least this many transport mean free paths in radius
     const float* mrw_k;            // [ncells] rhoL chi_t(T): inverse transport mean free path (scaled)
     const float* mrw_kp;           // [ncells] Planck-mean absorption coefficient kappa_P(T)
+    PeelEvent* peel_q;             // imaging pass, event kernel: queue of peel-off events, or null
+    unsigned long long* peel_n;    // events queued (may pass peel_cap: those were peeled inline)
+    int64_t peel_cap;
     uint64_t budget_ns;            // watchdog budget after the launch stamp, 0 = none
     int32_t regroup;               // event kernel: leave walk phase below this many walkers
     int32_t smem_sed;              // 1: SED tallies in shared memory

@@ -46,6 +46,9 @@ __device__ __forceinline__ bool past_deadline(const RunArgs& a, const Tallies& t
     return false;
 }
 
+// Optical depth beyond which a peel-off ray stops: exp(-40) = 4e-18 of its weight remains.
+constexpr float PEEL_TAU_STOP = 40.f;
+
 inline size_t shared_bytes(const PropagateJob& job) {
     if (!job.args.smem_sed) return 0;
     return sizeof(double) * (size_t)job.obs.nobs * job.obs.nsed + sizeof(unsigned) * (size_t)N_ESC_MU * job.obs.nsed;
