@@ -46,10 +46,13 @@ UNIT = "packets/s"
 B_CROSS = 20.0
 B_PEEL = 4.0
 B_REEMIT = 400.0
-# DRAM bytes (read + write) per propagation launch from an ncu capture of the current kernel on
-# a small case of this workload, averaged over a step's launch mix (10 Lucy, 1 imaging): the
-# first touch of the resident grid and tables, which does not grow with the packet count
-TRAFFIC_PER_LAUNCH = 0.78e6
+# DRAM bytes (read + write) per propagation launch, averaged over a step's 12 launches (10 Lucy
+# iterations, the imaging pass and its peel pass), from an ncu capture of the current kernels on
+# a 2e5-packet case of this workload scaled to 1e7 packets: the Lucy launches touch the resident
+# grid and tables once (0.58 MB, independent of the packet count); the peel-event queue (48 B
+# per event, 4.74e6 events) and its cell order grow with the packets: 228 MB written by the
+# imaging pass, 247 MB read by the peel pass
+TRAFFIC_PER_LAUNCH = 40.1e6
 
 
 def parse():
@@ -337,7 +340,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH if kern == hrt.HRT_KERNEL_EVENT else None,
                          "traffic_unit": "bytes per launch (ncu)", "peak_source": src,
-                         "kernel": "k_event (propagation)" if kern == hrt.HRT_KERNEL_EVENT else "k_plain",
+                         "kernel": "k_event + k_peel_rays (propagation)" if kern == hrt.HRT_KERNEL_EVENT else "k_plain",
                          "kernel_ms_per_step": kms, "algorithmic_bytes_per_step": byts},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rho_h.numel() * 4 + T0_h.numel() * 8),
                     "d2h_bytes_per_step": int(T_out.numel() * 8 + sed_out.numel() * 8)},
