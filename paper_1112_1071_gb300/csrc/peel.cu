@@ -14,6 +14,7 @@
 namespace hrt {
 
 constexpr int USCAN_BLOCK = 1024;
+constexpr int PEEL_MINB = 4;       // blocks of 256 per SM the registers are budgeted for (measured)
 
 namespace {
 
@@ -99,8 +100,8 @@ __global__ void k_peel_scatter(RunArgs a, int64_t ncells, uint32_t* __restrict__
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_peel_rays(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t,
-                                                   const uint32_t* __restrict__ order) {
+__global__ void __launch_bounds__(256, PEEL_MINB)
+    k_peel_rays(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t, const uint32_t* __restrict__ order) {
     const SharedTallies st = shared_tallies(o, a);
     LocalCounters lc;
     lc.zero();
