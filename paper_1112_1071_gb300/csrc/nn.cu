@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const bf16* __restrict__ i
         }
 }
 
-cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
-                         cudaStream_t s) {
+cudaError_t conv3d_wgrad_mma(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
+                             cudaStream_t s) {
     if (Cin % 8 != 0 || Cout % 8 != 0) return cudaErrorInvalidValue;
     const long long total = (long long)D * H * W * N;
     int nsplit = (int)(total / 4096);

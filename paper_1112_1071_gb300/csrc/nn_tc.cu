@@ -224,6 +224,194 @@ cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out,
     return launch_tc<32>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dW[tap][i][o] += sum_v in[v + off(tap)][i] dY[v][o]: per block a GEMM with M = 128 rows of
+// (tap, input channel) -- TPG = 128 / CB taps of a block of CB input channels --, N = BN output
+// channels and K = a contiguous range of voxels (split over blocks; FP32 atomics at the end).
+// Both operands are read voxel by voxel with their channels contiguous, the MN-major form:
+// every 16-byte load (8 channels of one voxel) is one row of a core matrix (8 voxels along K x 16
+// bytes along M or N), core matrices 128 bytes apart along K (the descriptor's leading byte
+// offset, as in the K-major operands of the convolution) and KV * 16 bytes apart along M/N (its
+// stride byte offset).
+// KV = 64 voxels per stage (four K = 16 MMAs), two stage buffers, one mbarrier per buffer.
+constexpr int WG_KV = 64;
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv3d_wgrad_tc(const bf16* __restrict__ in, const bf16* __restrict__ dy,
+                                                         float* __restrict__ dw, int D, int H, int W, int Cin, int Cout,
+                                                         int CB, int nsplit, int nbatch) {
+    constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
+    constexpr int A_BYTES = 128 * WG_KV * 2, B_BYTES = BN * WG_KV * 2;
+    constexpr int MN_STRIDE = WG_KV / 8 * 128;       // between 8-row groups along M (or N)
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sA = tc::smem_addr(smem);
+    const uint32_t sB = sA + 2 * A_BYTES;
+    const uint32_t bar0 = sB + 2 * B_BYTES;
+    const uint32_t slot = bar0 + 16;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int TPG = 128 / CB;                        // taps per block
+    const int ngroups = (27 + TPG - 1) / TPG;
+    const int tap0 = (blockIdx.x % ngroups) * TPG;
+    const int i0 = (blockIdx.x / ngroups) * CB;
+    const int o0 = blockIdx.y * BN;
+    const long long V = (long long)D * H * W, total = V * nbatch;
+    const long long per = ((total + nsplit - 1) / nsplit + WG_KV - 1) / WG_KV * WG_KV;
+    const long long vbeg = (long long)blockIdx.z * per;
+    const long long vend = vbeg + per < total ? vbeg + per : total;
+
+    if (warp == 0) {
+        tc::tmem_alloc(slot, NCOLS);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar0, 1);
+        tc::mbar_init(bar0 + 8, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot) : "memory");
+
+    // thread -> voxel kv = tid / 2 of the stage, row chunks (tid & 1) * 8 .. + 7 of the 16
+    const int kv = tid >> 1, rc0 = (tid & 1) * 8;
+    auto load = [&](long long v0, int buf) {
+        const long long v = v0 + kv;
+        const bool vin = v < vend;
+        int x = 0, y = 0, z = 0;
+        long long base = 0;
+        if (vin) {
+            const long long b = v / V, r = v - b * V;
+            x = (int)(r % W);
+            y = (int)((r / W) % H);
+            z = (int)(r / ((long long)W * H));
+            base = b * V;
+        }
+        const uint32_t a = sA + buf * A_BYTES + (kv >> 3) * 128 + (kv & 7) * 16;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int row0 = (rc0 + q) * 8;                 // first of the chunk's 8 rows
+            const int t = row0 / CB, tap = tap0 + t, i = i0 + row0 % CB;
+            bool ok = vin && t < TPG && tap < 27;
+            const bf16* src = in;
+            if (ok) {
+                const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+                ok = zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+                if (ok) src = in + (base + ((long long)zz * H + yy) * W + xx) * Cin + i;
+            }
+            cp_async16_zfill(a + (row0 >> 3) * MN_STRIDE, src, ok);
+        }
+        const uint32_t b = sB + buf * B_BYTES + (kv >> 3) * 128 + (kv & 7) * 16;
+        for (int ng = (tid & 1); ng < BN / 8; ng += 2) {
+            const bool ok = vin;
+            cp_async16_zfill(b + ng * MN_STRIDE, ok ? (const void*)(dy + v * Cout + o0 + ng * 8) : (const void*)dy, ok);
+        }
+        cp_async_commit();
+    };
+
+    // instruction descriptor: FP32 D, BF16 A and B, both MN-major (bits 15 and 16), M = 128, N = BN
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, BN) | (1u << 15) | (1u << 16);
+    const int S = (int)((vend - vbeg + WG_KV - 1) / WG_KV);
+    bool failed = false;
+    if (S > 0) load(vbeg, 0);
+    for (int s = 0; s < S; ++s) {
+        const int buf = s & 1;
+        cp_async_wait<0>();
+        tc::fence_proxy_async_smem();
+        if (__syncthreads_or(failed ? 1 : 0)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a = sA + buf * A_BYTES, b = sB + buf * B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < WG_KV / 16; ++kk)
+                tc::mma_bf16(tmem, tc::smem_desc(a + kk * 256, 128, MN_STRIDE), tc::smem_desc(b + kk * 256, 128, MN_STRIDE),
+                             IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_commit(bar0 + 8 * buf);
+        }
+        if (s + 1 < S) {
+            if (s >= 1 && !tc::mbar_wait(bar0 + 8 * (buf ^ 1), (uint32_t)((s - 1) >> 1) & 1u, WAIT_LIMIT_NS)) failed = true;
+            if (!failed) load(vbeg + (long long)(s + 1) * WG_KV, buf ^ 1);
+        }
+    }
+    if (!failed && S > 0 && !tc::mbar_wait(bar0 + 8 * ((S - 1) & 1), (uint32_t)((S - 1) >> 1) & 1u, WAIT_LIMIT_NS))
+        failed = true;
+    cp_async_wait<0>();
+    failed = __syncthreads_or(failed ? 1 : 0) != 0;
+    if (!failed && S > 0) {
+        tc::fence_after_sync();
+        const int t = tid / CB, tap = tap0 + t, i = i0 + tid % CB;
+        const bool valid = t < TPG && tap < 27;
+        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float acc[16];
+            tc::tmem_ld16(row_addr + (uint32_t)c0, acc);
+            if (valid) {
+                float* dst = dw + ((long long)tap * Cin + i) * Cout + o0 + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) atomicAdd(dst + j, acc[j]);
+            }
+        }
+    } else if (failed && tid == 0) {
+        atomicExch(&g_tc_error, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+template <int BN>
+static cudaError_t launch_wgrad_tc(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin,
+                                   int Cout, int CB, cudaStream_t s) {
+    constexpr int NCOLS = BN < 32 ? 32 : BN;
+    constexpr int MAX_RESIDENT = 512 / NCOLS;
+    static int smem = 0;
+    if (smem == 0) {
+        int bytes = 2 * (128 + BN) * WG_KV * 2 + 32;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv3d_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        for (;;) {
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_wgrad_tc<BN>, 128, bytes);
+            if (e != cudaSuccess) return e;
+            if (per_sm <= MAX_RESIDENT) break;
+            bytes += 4096;
+            if (bytes > 200 * 1024) return cudaErrorInvalidConfiguration;
+        }
+        smem = bytes;
+    }
+    const int TPG = 128 / CB;
+    const int blocks_mn = ((27 + TPG - 1) / TPG) * (Cin / CB) * (Cout / BN);
+    const long long total = (long long)D * H * W * N;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // voxel splits: enough blocks for four waves, at least 8 stages per block
+    long long nsplit = ((long long)sms * 8 + blocks_mn - 1) / blocks_mn;
+    const long long max_split = (total + 8 * WG_KV - 1) / (8 * WG_KV);
+    if (nsplit > max_split) nsplit = max_split;
+    if (nsplit < 1) nsplit = 1;
+    const dim3 grid((unsigned)(((27 + TPG - 1) / TPG) * (Cin / CB)), (unsigned)(Cout / BN), (unsigned)nsplit);
+    k_conv3d_wgrad_tc<BN><<<grid, 128, smem, s>>>(in, dy, dw, D, H, W, Cin, Cout, CB, (int)nsplit, N);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
+                         cudaStream_t s) {
+    // channel blocks of CB <= 128 rows stacked with 128 / CB taps; other shapes on mma.sync
+    const int CB = Cin <= 128 ? Cin : 64;
+    if (Cin % 16 != 0 || Cout % 32 != 0 || Cin % CB != 0 || 128 % CB != 0 && Cin > 128)
+        return conv3d_wgrad_mma(in, dy, dw, N, D, H, W, Cin, Cout, s);
+    if (Cout % 128 == 0) return launch_wgrad_tc<128>(in, dy, dw, N, D, H, W, Cin, Cout, CB, s);
+    if (Cout % 64 == 0) return launch_wgrad_tc<64>(in, dy, dw, N, D, H, W, Cin, Cout, CB, s);
+    return launch_wgrad_tc<32>(in, dy, dw, N, D, H, W, Cin, Cout, CB, s);
+}
+
 cudaError_t tc_status(int* failed, cudaStream_t s) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;

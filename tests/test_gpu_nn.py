@@ -50,10 +50,13 @@ def test_conv3d_forward_matches_oracle(cin, cout, relu):
         close(got[s], ref, 8e-3)      # one BF16 rounding of the output
 
 
-def test_conv3d_backward_matches_oracle():
+@pytest.mark.parametrize("cin,cout", [(32, 64), (64, 128), (96, 32), (192, 64)])
+def test_conv3d_backward_matches_oracle(cin, cout):
+    # weight gradients on tcgen05: 4, 2, 1 taps of all input channels and (192) 2 taps of 64-channel
+    # blocks stacked into the MMA's 128 rows
     torch = torch_cuda()
     rng = np.random.default_rng(7)
-    n, d, h, w, cin, cout = 2, 4, 6, 8, 32, 64
+    n, d, h, w = 2, 4, 6, 8
     x = bf16(rng.normal(size=(n, d, h, w, cin)))
     wt = bf16(rng.normal(size=(3, 3, 3, cin, cout)) / np.sqrt(27 * cin))
     g = bf16(rng.normal(size=(n, d, h, w, cout)))
