@@ -22,6 +22,11 @@ time_to_converged_ms      device time of the Lucy iterations until the 99th perc
 time_to_converged_pda_ms  the same from a separate solve (not in `value`) in which cells entered
           by fewer than --pda-min packets take the partial diffusion approximation (App. A).
 
+``--rows`` instead measures the extensions of the method on their own workloads (one JSON line, not
+the headline): the modified random walk against the plain walk on thick grey models and an
+embedded envelope, raytracing against peel-off in the disk's imaging pass, Lucy iterations on the
+cylindrical disk and the clouds in an external radiation field.
+
 ``--impl reference`` times the FP64 CPU oracle (the reference implementation of this build) on
 the host cores on a bounded sample of the same workload.  N > 1 GPUs (torchrun) run independent
 disk models, one per rank (weak scaling, no collective).
@@ -66,6 +71,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", action="store_true",
+                    help="measure the extension rows (MRW, raytracing, cylindrical grids, external field) instead")
     ap.add_argument("--pda-min", type=int, default=6000,
                     help="packet entries below which a cell takes the diffusion approximation in the "
                          "time-to-converged solve with PDA (App. A); 0 skips that solve")
@@ -200,6 +207,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.rows:
+        return rows_bench(local)
 
     import numpy as np
     import torch
@@ -356,6 +365,71 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def rows_bench(local):
+    """Device times (ms_propagate, CUDA events on the library stream) of the extension rows."""
+    import numpy as np
+    import torch
+    from paper_1112_1071_gb300 import hrt
+    from paper_1112_1071_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    out = {}
+
+    # modified random walk: thick grey models, 1e6 packets, 2nd iteration, gamma 2 / 4 / off
+    mrw = {}
+    for kind in ("cartesian", "spherical", "cylindrical"):
+        wl = W.thick_grey(kind, 1_000_000)
+        rows, T = {}, {}
+        for gamma in (2.0, 4.0, 0.0):
+            m = hrt.Model(wl, device=local)
+            for _ in range(2):
+                st = m.run_iteration(mrw_gamma=gamma, watchdog_ms=120000)
+            rows[f"gamma_{gamma:g}"] = {"ms": st["ms_propagate"], "interactions_per_packet": st["n_interactions"] / 1e6,
+                                        "mrw_steps_per_packet": st["n_mrw"] / 1e6, "killed": st["n_killed"]}
+            T[gamma] = m.temperature()
+        for gamma in (2.0, 4.0):
+            d = (T[gamma] - T[0.0]) / T[0.0]
+            rows[f"gamma_{gamma:g}"]["dT_vs_plain_mean"] = float(np.abs(d).mean())
+        mrw[kind] = rows
+    # embedded envelope, tau_550 = 1e5, 1e5 packets, 5 iterations from 10 K
+    env = {}
+    for gamma in (2.0, 0.0):
+        m = hrt.Model(W.embedded_envelope(tau_550=1e5, n_packets=100_000), device=local)
+        ms, killed = 0.0, 0
+        for _ in range(5):
+            st = m.run_iteration(mrw_gamma=gamma, watchdog_ms=120000)
+            ms += st["ms_propagate"]
+            killed = st["n_killed"]
+        env[f"gamma_{gamma:g}"] = {"ms_5_iterations": ms, "killed_last_iteration": killed,
+                                   "interactions_per_packet_last": st["n_interactions"] / 1e5}
+    mrw["embedded_envelope_tau1e5"] = env
+    out["mrw"] = mrw
+
+    # raytracing against peel-off in the disk's imaging pass (1e7 packets, 1e6 dust rays)
+    m = hrt.Model(W.flared_disk(n_packets=10_000_000), device=local)
+    for _ in range(4):
+        m.run_iteration()
+    rt = {}
+    for rays in (0, 1_000_000):
+        st = m.run_iteration(peel=1, update_temperature=0)
+        st = m.run_iteration(peel=1, update_temperature=0, raytrace_rays=rays)
+        rt[f"rays_{rays}"] = {"ms": st["ms_total"], "peel_crossings": st["n_peel_crossings"]}
+    out["raytracing_disk"] = rt
+
+    # Lucy iterations on the cylindrical disk (with external field) and the ISRF clouds
+    lucy = {}
+    for name, wl in (("cylindrical_disk_isrf", W.cylindrical_disk(n_packets=10_000_000, isrf_dilution=1e-13)),
+                     ("isrf_cloud_cartesian", W.isrf_cloud("cartesian", n=64, tau_550=3.0, n_packets=10_000_000)),
+                     ("isrf_cloud_spherical", W.isrf_cloud("spherical", n=64, tau_550=3.0, n_packets=10_000_000)),
+                     ("isrf_cloud_cylindrical", W.isrf_cloud("cylindrical", n=64, tau_550=3.0, n_packets=10_000_000))):
+        m = hrt.Model(wl, device=local)
+        for _ in range(3):
+            st = m.run_iteration()
+        lucy[name] = {"ms": st["ms_propagate"], "packets_per_s": wl.n_packets / (st["ms_propagate"] * 1e-3),
+                      "crossings_per_s": st["n_crossings"] / (st["ms_propagate"] * 1e-3)}
+    out["lucy_iterations"] = lucy
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

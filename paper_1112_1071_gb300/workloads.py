@@ -397,6 +397,39 @@ def embedded_envelope(n_r: int = 60, n_theta: int = 8, tau_550: float = 1e5, r_i
                     obs_az=np.zeros(10), n_packets=n_packets, seed=seed)
 
 
+def thick_grey(kind: str = "cartesian", n_packets: int = 3000, tau_cell: float | None = None) -> Workload:
+    """Optically thick grey models whose cells are many transport mean free paths across (the
+    modified random walk's regime, Sect. 2.2): grey dust (chi = 1 cm^2/g, albedo 0.5, g = 0.6).
+    "cartesian": 4^3 cells over +-100 AU, 60 extinction mean free paths per cell (tau_cell), a
+    5800 K 1 Lsun star off-centre; "spherical": r walls 5, 20, 45, 80, 100 AU (a hole), 4 cones,
+    3 wedges, tau_cell per 20 AU (default 50); "cylindrical": R walls 0, 20, 45, 80, 100 AU, z
+    walls -60, -20, 20, 60 AU, one phi cell, tau_cell per 20 AU (default 50); stars at the origin
+    except for the cube."""
+    nu, chi, alb, g = dust_table()
+    chi = np.full_like(nu, 1.0)
+    alb = np.full_like(nu, 0.5)
+    src = [dict(pos=(0.0, 0.0, 0.0), L=LSUN, Teff=5800.0)]
+    if kind == "cartesian":
+        w = np.linspace(-100 * AU, 100 * AU, 5)
+        walls = [w, w.copy(), w.copy()]
+        rho = np.float32((60.0 if tau_cell is None else tau_cell) / (50 * AU))
+        src = [dict(pos=(AU, 2 * AU, 3 * AU), L=LSUN, Teff=5800.0)]
+    elif kind == "spherical":
+        walls = [np.array([5.0, 20.0, 45.0, 80.0, 100.0]) * AU, np.array([0.0, 0.9, math.pi / 2, 2.2, math.pi]),
+                 np.array([0.0, 2.0, 4.0, 2 * math.pi])]
+        rho = np.float32((50.0 if tau_cell is None else tau_cell) / (20 * AU))
+    elif kind == "cylindrical":
+        walls = [np.array([0.0, 20.0, 45.0, 80.0, 100.0]) * AU, np.array([-60.0, -20.0, 20.0, 60.0]) * AU,
+                 np.array([0.0, 2 * math.pi])]
+        rho = np.float32((50.0 if tau_cell is None else tau_cell) / (20 * AU))
+    else:
+        raise ValueError(kind)
+    shape = tuple(len(x) - 1 for x in walls)[::-1]
+    return Workload(name=f"thick_{kind}", grid_type=kind, walls=walls, rho=np.full(shape, rho, np.float32), nu=nu,
+                    chi=chi, albedo=alb, g=g, T_nodes=temperature_nodes(), sources=src,
+                    obs_incl=np.radians([30.0]), obs_az=np.zeros(1), n_packets=n_packets, seed=21)
+
+
 WORKLOADS = {
     "tiny_sphere": tiny_sphere,
     "flared_disk": flared_disk,

@@ -63,36 +63,16 @@ def test_mrw_path_matches_oracle():
     np.testing.assert_allclose(got, want, rtol=2e-6)
 
 
-def _grey(wl):
-    wl.chi = np.full_like(wl.nu, 1.0)
-    wl.albedo = np.full_like(wl.nu, 0.5)
-    return wl
-
-
 def _thick(kind, n_packets=3000):
-    """Optically thick models whose cells are many transport mean free paths across."""
-    AU = W.AU
-    if kind == "cartesian":
-        w = np.linspace(-100 * AU, 100 * AU, 5)
-        wl = workload_from_walls("cartesian", [w, w.copy(), w.copy()], rho=np.ones((4, 4, 4), np.float32))
-        wl.sources = [dict(pos=(AU, 2 * AU, 3 * AU), L=W.LSUN, Teff=5800.0)]
-        wl = _grey(wl)
-        wl.rho[:] = np.float32(60.0 / (50 * AU))              # 60 extinction mean free paths per cell
-    elif kind == "spherical":
-        walls = [np.array([5.0, 20.0, 45.0, 80.0, 100.0]) * AU, np.array([0.0, 0.9, math.pi / 2, 2.2, math.pi]),
-                 np.array([0.0, 2.0, 4.0, 2 * math.pi])]
-        wl = _grey(workload_from_walls("spherical", walls, rho=np.ones((3, 4, 4), np.float32)))
-        wl.rho[:] = np.float32(50.0 / (20 * AU))
-    elif kind == "cylindrical":
-        walls = [np.array([0.0, 20.0, 45.0, 80.0, 100.0]) * AU, np.array([-60.0, -20.0, 20.0, 60.0]) * AU,
-                 np.array([0.0, 2 * math.pi])]
-        wl = _grey(workload_from_walls("cylindrical", walls, rho=np.ones((1, 3, 4), np.float32)))
-        wl.rho[:] = np.float32(50.0 / (20 * AU))
-    else:   # non-grey: the synthetic dust, thick at the temperatures reached (chi_t, kappa_P vary with T)
-        w = np.linspace(-100 * AU, 100 * AU, 5)
-        wl = workload_from_walls("cartesian", [w, w.copy(), w.copy()], rho=np.ones((4, 4, 4), np.float32))
-        wl.sources = [dict(pos=(AU, 2 * AU, 3 * AU), L=W.LSUN, Teff=5800.0)]
-        wl.rho[:] = np.float32(1e5 / (W.chi_at_lambda_um(0.55) * 50 * AU))
+    """Optically thick models whose cells are many transport mean free paths across: the grey
+    models of the workloads module, and a non-grey cube (the synthetic dust, thick at the
+    temperatures reached: chi_t and kappa_P vary with T)."""
+    if kind != "nongrey":
+        return W.thick_grey(kind, n_packets)
+    w = np.linspace(-100 * W.AU, 100 * W.AU, 5)
+    wl = workload_from_walls("cartesian", [w, w.copy(), w.copy()], rho=np.ones((4, 4, 4), np.float32))
+    wl.sources = [dict(pos=(W.AU, 2 * W.AU, 3 * W.AU), L=W.LSUN, Teff=5800.0)]
+    wl.rho[:] = np.float32(1e5 / (W.chi_at_lambda_um(0.55) * 50 * W.AU))
     wl.n_packets = n_packets
     return wl
 
@@ -100,12 +80,9 @@ def _thick(kind, n_packets=3000):
 def _moderate(kind, n_packets=3000):
     """Cells of 3-6 extinction mean free paths: with gamma = 1 (2 for the non-grey model) the
     packets take ~5 MRW steps each, short chains that stay in lockstep."""
-    wl = _thick(kind, n_packets)
-    if kind == "cartesian":
-        wl.rho[:] = np.float32(6.0 / (50 * W.AU))
-    elif kind in ("spherical", "cylindrical"):
-        wl.rho[:] = np.float32(3.0 / (20 * W.AU))
-    return wl, (2.0 if kind == "nongrey" else 1.0)
+    if kind == "nongrey":
+        return _thick(kind, n_packets), 2.0
+    return W.thick_grey(kind, n_packets, tau_cell=6.0 if kind == "cartesian" else 3.0), 1.0
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
