@@ -426,10 +426,10 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     PropagateJob j = job;
     const bool peel = job.args.peel != 0;
     // default shapes (measured on GB300): 3 blocks of 256 per SM (80 registers); warps stay in
-    // the walk phase while at least 20 (spherical Lucy iteration) or 24 (imaging pass; Cartesian
-    // runs of >= 4M packets) lanes walk, 12 for small Cartesian runs whose tail dominates
+    // the walk phase while at least 24 lanes walk (curvilinear grids; Cartesian runs of >= 4M
+    // packets), 12 for small Cartesian runs whose tail dominates
     int rg_default = DEFAULT_REGROUP;
-    if (job.grid.type != GRID_CARTESIAN) rg_default = peel ? 24 : 20;
+    if (job.grid.type != GRID_CARTESIAN) rg_default = 24;
     else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 24;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
