@@ -374,7 +374,11 @@ int hrt_batch_destroy(hrt_batch* b);
 /* Run up to max_iter Lucy iterations for every unconverged model, n_packets[m] packets each,
  * one persistent launch per iteration (captured as a CUDA graph after the first).  Writes the
  * last stats of every model to per_model_out[n] (may be NULL) and the number of iterations run
- * to *iterations_run (may be NULL). */
+ * to *iterations_run (may be NULL).  Models are Cartesian or spherical-polar (hrt_batch_create
+ * returns HRT_EINVAL for others).  params: the convergence settings, max_interactions,
+ * terminate_on_absorb and watchdog_ms apply; peel-off, imaging passes, the PDA, raytracing and
+ * the modified random walk run in single-model calls (mrw_gamma != 0, pda_min_visits != 0,
+ * raytrace_rays != 0, peel != 0 or update_temperature == 0 return HRT_EINVAL). */
 int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hrt_run_params* params,
                   hrt_iter_stats* per_model_out, int* iterations_run);
 /* Time a few launch shapes on one iteration's worth of work and keep the fastest. */

@@ -377,7 +377,9 @@ int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hr
     if (params) P = *params;
     else hrt_default_params(&P);
     if (!(P.p > 0 && P.p <= 1) || P.max_interactions < 0) return HRT_EINVAL;
-    if (P.mrw_gamma != 0) return HRT_EINVAL;     // the modified random walk runs in single-model calls
+    // Lucy iterations only: the extensions and imaging passes run in single-model calls
+    if (P.mrw_gamma != 0 || P.pda_min_visits != 0 || P.raytrace_rays != 0 || P.peel != 0 || !P.update_temperature)
+        return HRT_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);

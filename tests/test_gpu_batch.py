@@ -76,3 +76,18 @@ def test_batch_tune_picks_a_shape_and_caches_it():
     assert L.hrt_batch_run(b, npk.ctypes.data, 2, None, stats, C.byref(iters)) == 0
     assert iters.value >= 1
     L.hrt_batch_destroy(b)
+
+
+@pytest.mark.parametrize("field,value", [("mrw_gamma", 2.0), ("pda_min_visits", 100), ("raytrace_rays", 1000),
+                                         ("peel", 1), ("update_temperature", 0)])
+def test_batch_rejects_settings_of_single_model_calls(field, value):
+    # a batch runs Lucy iterations; the extensions and imaging passes are single-model calls
+    L = hrt.load()
+    wls = W.batched_disks(n_models=2, size_scale=0.1, packet_scale=0.001, seed=7)
+    models = [hrt.Model(wl) for wl in wls]
+    b = _batch(models)
+    npk = np.array([wl.n_packets for wl in wls], np.int64)
+    p = hrt.default_params(**{field: value})
+    assert L.hrt_batch_run(b, npk.ctypes.data, 1, C.byref(p), None, None) == hrt.HRT_EINVAL
+    assert L.hrt_batch_run(b, npk.ctypes.data, 1, None, None, None) == 0
+    L.hrt_batch_destroy(b)
