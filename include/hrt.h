@@ -182,6 +182,11 @@ typedef struct {
                                     counts as one interaction against max_interactions.  Single-model
                                     runs only (a batch returns HRT_EINVAL).  0 (default) = off;
                                     finite, >= 0 */
+    int64_t peel_queue_events;   /* imaging passes with the event kernel queue their peel-off events for
+                                    a separate peel pass (48 bytes each); this caps the queue (0 =
+                                    default: 2 per packet, at least 2^20, at most 2^27); events past
+                                    the cap are peeled inline by the propagation kernel (same
+                                    results, slower); >= 0 */
 } hrt_run_params;
 
 typedef struct {

@@ -729,6 +729,7 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         return ctx->fail(HRT_EINVAL, "raytrace_rays must be in [0, 2^32)");
     if (!(P.mrw_gamma >= 0) || !std::isfinite(P.mrw_gamma))
         return ctx->fail(HRT_EINVAL, "mrw_gamma must be finite and >= 0");
+    if (P.peel_queue_events < 0) return ctx->fail(HRT_EINVAL, "peel_queue_events must be >= 0");
     const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
     if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
         return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");
@@ -832,11 +833,13 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (A.peel && P.kernel != HRT_KERNEL_PLAIN && ctx->grid.n1 < 32768 && ctx->grid.n2 < 32768 && ctx->grid.n3 < 32768) {
         // queue for the peel pass (16-bit cell indices per axis): two events per packet (an
         // overflow is peeled inline), at most 2^27 events (6 GiB)
-        const int64_t cap = std::min<int64_t>(std::max<int64_t>(2 * n_packets, (int64_t)1 << 20), (int64_t)1 << 27);
+        const int64_t cap = P.peel_queue_events > 0
+                                ? std::min<int64_t>(P.peel_queue_events, (int64_t)1 << 27)
+                                : std::min<int64_t>(std::max<int64_t>(2 * n_packets, (int64_t)1 << 20), (int64_t)1 << 27);
         if (ctx->d_peel_q.n < (size_t)cap) CK(ctx->d_peel_q.alloc((size_t)cap), "peel queue");
         job.args.peel_q = ctx->d_peel_q.p;
         job.args.peel_n = ctx->d_work.p + 2;
-        job.args.peel_cap = (int64_t)ctx->d_peel_q.n;
+        job.args.peel_cap = cap;
     }
     cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
                                                  : launch_propagate_event(job, L, s, &launched);

@@ -39,6 +39,7 @@ class hrt_run_params(C.Structure):
         ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("regroup_threshold", C.c_int32),
         ("watchdog_ms", C.c_double), ("first_packet", C.c_int64), ("n_total", C.c_int64),
         ("pda_min_visits", C.c_int64), ("raytrace_rays", C.c_int64), ("mrw_gamma", C.c_double),
+        ("peel_queue_events", C.c_int64),
     ]
 
 

@@ -232,3 +232,28 @@ def test_event_kernel_reproduces_plain_histories(name):
     np.testing.assert_allclose(sg.sum(axis=1), sr.sum(axis=1), rtol=1e-4)
     big = sr > 1e-3 * sr.max()
     np.testing.assert_allclose(sg[big], sr[big], rtol=1e-3)
+
+
+@pytest.mark.parametrize("name", ["tiny_sphere", "flared_disk"])
+def test_peel_queue_overflow_is_peeled_inline_with_the_same_result(name):
+    # an imaging pass queues its peel-off events for the peel pass; events past the queue's
+    # capacity are walked by the propagation kernel itself: the same rays, the same weights
+    wl = W.WORKLOADS[name](n_packets=100_000)
+    if name == "flared_disk":
+        wl = W.flared_disk(n_packets=100_000, n_r=80, n_theta=48)
+        wl.img_nx = wl.img_ny = 32
+        wl.img_half_extent = 300 * W.AU
+        wl.img_lam_um = np.array([1.0, 100.0])
+    runs = []
+    for cap in (0, 1000):
+        m = hrt.Model(wl)
+        m.run_iteration()
+        st = m.run_iteration(peel=1, update_temperature=0, peel_queue_events=cap)
+        runs.append((st, m.sed(), m.image() if wl.img_nx > 0 else None))
+    (s0, sed0, img0), (s1, sed1, img1) = runs
+    assert s1["n_peel_crossings"] == s0["n_peel_crossings"] and s1["n_crossings"] == s0["n_crossings"]
+    np.testing.assert_allclose(sed1, sed0, rtol=1e-9, atol=1e-300)
+    if img0 is not None:
+        np.testing.assert_allclose(img1, img0, rtol=1e-9, atol=1e-300)
+    with pytest.raises(hrt.HrtError):
+        hrt.Model(wl).run_iteration(peel=1, update_temperature=0, peel_queue_events=-1)
