@@ -195,11 +195,12 @@ static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, 
                              int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     constexpr int NCOLS = BN < 32 ? 32 : BN;
     constexpr int MAX_RESIDENT = 512 / NCOLS;
+    // the attribute belongs to the current device's context: set it on every launch
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
     static int smem = 0;
     if (smem == 0) {
         int bytes = smem_bytes<BN>();
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
         for (;;) {
             int per_sm = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_tc<BN>, 128, bytes);
@@ -369,12 +370,11 @@ static cudaError_t launch_wgrad_tc(const bf16* in, const bf16* dy, float* dw, in
                                    int Cout, int CB, cudaStream_t s) {
     constexpr int NCOLS = BN < 32 ? 32 : BN;
     constexpr int MAX_RESIDENT = 512 / NCOLS;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
     static int smem = 0;
     if (smem == 0) {
         int bytes = 2 * (128 + BN) * WG_KV * 2 + 32;
-        cudaError_t e =
-            cudaFuncSetAttribute(k_conv3d_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
         for (;;) {
             int per_sm = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_wgrad_tc<BN>, 128, bytes);
