@@ -11,7 +11,7 @@ temperature of unseen clouds, and the iteration restarted from that prediction i
 with the cold start on (a) the distance to a reference solution, mean |T - T*| / T* (T* the
 average of the late iterations of an independent long run), and (b) the convergence test of
 the method, the 99th percentile of the iteration change in T below 2 %.  The Monte-Carlo
-iteration and its convergence test stay the judge.
+iteration and its convergence test decide the result.
 
     python -m paper_1112_1071_gb300.learned --n 64 --train 256 --test 8
 """
