@@ -301,7 +301,7 @@ int hrt_get_visits(hrt_ctx* ctx, uint32_t* out, int64_t n);
 /* ------------------------------------------------------------------ learned warm start
  * Not in the paper: a 3-D convolutional encoder-decoder (U-Net) trained on temperature fields
  * that the Monte-Carlo iteration itself produced, used only to start the iteration closer to its
- * fixed point; the Lucy iteration and its convergence test (Sect. 2.3-2.4) stay the judge.
+ * fixed point; the Lucy iteration and its convergence test (Sect. 2.3-2.4) decide the result.
  * Levels L (1-4), base width c (multiple of 32): per level two 3x3x3 conv+ReLU and 2x average
  * pooling, a bottleneck of width c 2^L, a mirrored decoder (2x nearest upsampling concatenated
  * with the encoder skip, two conv+ReLU) and a 1x1x1 head.  Weights are FP32 masters (Adam) with
