@@ -2,20 +2,24 @@
  * hrt.h - C ABI of the GB300 Monte-Carlo dust continuum radiative transfer library (libhrt).
  *
  * The library computes the iterative LTE dust temperature of Robitaille (2011), HYPERION,
- * Sects. 2.2-2.6: photon packets are emitted from point and cell sources, propagated
- * through a Cartesian or spherical-polar grid of constant-density cells to a sampled
- * optical depth, scattered (Henyey-Greenstein) or absorbed and re-emitted, and the path
- * lengths they travel give the absorbed energy rate of every cell (Eq. 2); the cell
- * temperatures follow from the Planck-mean balance (Eq. 3), the iteration is repeated
- * until the percentile test of Sect. 2.4 (Eqs. 4-6) passes, and SEDs and images are
- * formed by peeling-off (Sect. 2.6.2).
+ * Sects. 2.2-2.6: photon packets are emitted from point, cell and external isotropic sources
+ * (Sect. 2.1.1), propagated through a Cartesian, spherical-polar or cylindrical-polar grid of
+ * constant-density cells (Sect. 2.1.2) to a sampled optical depth, scattered
+ * (Henyey-Greenstein) or absorbed and re-emitted, and the path lengths they travel give the
+ * absorbed energy rate of every cell (Eq. 2); the cell temperatures follow from the
+ * Planck-mean balance (Eq. 3), the iteration is repeated until the percentile test of
+ * Sect. 2.4 (Eqs. 4-6) passes, and SEDs and images are formed by peeling-off (Sect. 2.6.2).
+ * Optional parts of the method on the same path: the modified random walk in optically thick
+ * cells (Sect. 2.2), the partial diffusion approximation for poorly sampled cells (App. A) and
+ * raytracing of source and dust emission (Sect. 2.6.3); all are selected in hrt_run_params.
  *
  * Conventions (all entry points)
  *   - Every function returns 0 (HRT_OK) or a negative hrt_status; hrt_last_error() holds a
  *     one-line message for the last failure on that context.
  *   - Units are cgs: lengths cm, angles rad, frequencies Hz, luminosities erg/s, densities
  *     g/cm^3, opacities cm^2/g, temperatures K.  The emission time step is dt = 1 s.
- *   - Cell arrays are C-ordered [n3][n2][n1]: Cartesian [z][y][x], spherical [phi][theta][r].
+ *   - Cell arrays are C-ordered [n3][n2][n1]: Cartesian [z][y][x], spherical [phi][theta][r],
+ *     cylindrical [phi][z][R].
  *   - Host input arrays are copied; the caller keeps ownership and may free them on return.
  *     Host output arrays are caller-owned and must hold at least the stated count n
  *     (HRT_EINVAL otherwise).  *_device variants take device pointers and are ordered on the
@@ -226,8 +230,9 @@ int hrt_get_temperature(hrt_ctx* ctx, double* out, int64_t n);        /* K, [cel
 int hrt_get_specific_energy(hrt_ctx* ctx, double* out, int64_t n);    /* Adot, erg/s/g, [cells] */
 int hrt_get_absorbed(hrt_ctx* ctx, double* out, int64_t n);           /* raw sum eps kappa l, [cells] */
 int hrt_get_sed(hrt_ctx* ctx, double* out, int64_t n);                /* [nobs][nsed] erg/s/sr */
-int hrt_get_image(hrt_ctx* ctx, double* out, int64_t n);              /* [nobs][nimg][ny][nx] */
-int hrt_get_escape(hrt_ctx* ctx, double* out, int64_t n);             /* [10 cos(theta) bins][nsed] erg/s */
+int hrt_get_image(hrt_ctx* ctx, double* out, int64_t n);              /* [nobs][nimg][ny][nx] erg/s/sr per pixel */
+int hrt_get_escape(hrt_ctx* ctx, double* out, int64_t n);             /* [10 cos(theta) bins][nsed] erg/s, all
+                                                                         escaping packets of the last call (Sect. 2.6.1) */
 int hrt_get_temperature_device(hrt_ctx* ctx, double* d_out, int64_t n);
 int hrt_get_sed_device(hrt_ctx* ctx, double* d_out, int64_t n);
 int64_t hrt_num_cells(const hrt_ctx* ctx);
