@@ -811,6 +811,12 @@ static void place_in_cell(const or_model* m, const int c[3], double f0, double f
     }
 }
 
+/* Test hook: the point place_in_cell gives for cell c[3] and fractions f[3] in (0, 1]. */
+void or_place_in_cell(const or_model* m, const int32_t c[3], const double f[3], double p[3]) {
+    int ci[3] = {c[0], c[1], c[2]};
+    place_in_cell(m, ci, f[0], f[1], f[2], p);
+}
+
 /* Parameter t >= 0 at which the ray p + t u first enters the grid's outer boundary (0 when p is
  * already inside), or -1 when it misses the grid. */
 static double grid_entry(const or_model* m, const double p[3], const double u[3]) {

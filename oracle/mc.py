@@ -120,6 +120,8 @@ def _declare(L):
     L.or_sed_bin.restype = C.c_int
     L.or_wall_distance.argtypes = [C.POINTER(ORModel), _dp, _ip]
     L.or_wall_distance.restype = C.c_double
+    L.or_place_in_cell.argtypes = [C.POINTER(ORModel), _ip, _dp, _dp]
+    L.or_place_in_cell.restype = None
     L.or_mrw_path.argtypes = [C.c_double, C.c_double]
     L.or_mrw_path.restype = C.c_double
     L.or_run_packets.argtypes = [C.POINTER(ORModel), C.POINTER(ORParams), C.POINTER(ORResult)]
