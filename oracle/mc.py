@@ -192,7 +192,9 @@ class OracleModel:
         ext = list(getattr(wl, "external_sources", []) or [])
         Ls = [float(s["L"]) for s in wl.sources] + [float(e["L"]) for e in ext]
         self.src_pos = np.ascontiguousarray([s["pos"] for s in wl.sources], dtype=np.float64).reshape(-1)
-        teffs = [float(s["Teff"]) for s in wl.sources] + [float(e["Teff"]) for e in ext]
+        # a point source's spectrum: a blackbody of Teff, or its own f_nu ("spectrum": (nu, f_nu))
+        spectra = [("user", s["spectrum"]) if "spectrum" in s else ("bb", float(s["Teff"])) for s in wl.sources]
+        spectra += [("bb", float(e["Teff"])) for e in ext]
         self.next = len(ext)
         self.ext_c = np.ascontiguousarray([e["center"] for e in ext], dtype=np.float64).reshape(-1)
         self.ext_R = np.ascontiguousarray([e["radius"] for e in ext], dtype=np.float64)
@@ -204,7 +206,7 @@ class OracleModel:
         if wl.cell_source is not None:
             Lc = np.asarray(wl.cell_source["L"], dtype=np.float64).reshape(-1)
             Ls.append(float(Lc.sum()))
-            teffs.append(float(wl.cell_source["Teff"]))
+            spectra.append(("bb", float(wl.cell_source["Teff"])))
             cc = np.cumsum(Lc)
             self.cell_cdf = np.ascontiguousarray(cc / cc[-1])
             self.cell_cdf[-1] = 1.0
@@ -212,7 +214,8 @@ class OracleModel:
         cs = np.cumsum(Ls)
         self.src_cdf = np.ascontiguousarray(cs / cs[-1])
         self.src_cdf[-1] = 1.0
-        specs = [T.source_spectrum(self.nu[0], self.nu[-1], t) for t in teffs]
+        specs = [T.source_spectrum(self.nu[0], self.nu[-1], v) if kind == "bb"
+                 else T.user_source_spectrum(self.nu[0], self.nu[-1], *v) for kind, v in spectra]
         self.spec_nu = np.ascontiguousarray(specs[0][0])
         self.spec_cdf = np.ascontiguousarray(np.stack([s[1] for s in specs]))
         # observers

@@ -200,6 +200,34 @@ def source_spectrum(nu_min, nu_max, Teff, n=1000):
     return nu, cumulative_cdf(nu, planck_bnu(nu, Teff))
 
 
+def user_spectrum_at(v, unu, ufnu):
+    """A source's own spectrum f_nu, given at its nodes unu (strictly increasing, f >= 0),
+    evaluated at frequency v: a power law between two nodes (log-log interpolation), a straight
+    line where either of the two values is zero, and zero outside the nodes."""
+    if v < unu[0] or v > unu[-1]:
+        return 0.0
+    j = min(int(np.searchsorted(unu, v, side="right")) - 1, len(unu) - 2)
+    a, b = float(ufnu[j]), float(ufnu[j + 1])
+    if a > 0 and b > 0:
+        t = math.log(v / unu[j]) / math.log(unu[j + 1] / unu[j])
+        return math.exp((1 - t) * math.log(a) + t * math.log(b))
+    return a + (b - a) * (v - unu[j]) / (unu[j + 1] - unu[j])
+
+
+def user_source_spectrum(nu_min, nu_max, unu, ufnu, n=1000):
+    """A source with its own spectrum on the n log-spaced frequencies of the source grid over the
+    dust band, as (nodes, cdf); the cdf renormalises the in-band part to carry all of the
+    luminosity (Sect. 2.1.1: a source has a luminosity and a spectrum)."""
+    k = np.arange(n, dtype=np.float64)
+    nu = nu_min * (nu_max / nu_min) ** (k / (n - 1))
+    nu[0] = nu_min
+    nu[-1] = nu_max
+    unu = np.asarray(unu, dtype=np.float64)
+    ufnu = np.asarray(ufnu, dtype=np.float64)
+    f = np.array([user_spectrum_at(v, unu, ufnu) for v in nu])
+    return nu, cumulative_cdf(nu, f)
+
+
 def observer_frames(incl, az):
     """Observer unit vectors n = (sin i cos phi, sin i sin phi, cos i) and sky axes
     e_x = (-sin phi, cos phi, 0), e_y = n x e_x."""

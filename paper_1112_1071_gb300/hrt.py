@@ -225,7 +225,12 @@ class Model:
         check(self.ctx, L.hrt_set_dust(self.ctx, len(nu), _ptr(nu), _ptr(chi), _ptr(alb), float(wl.g), len(Tn), _ptr(Tn)))
         for s in wl.sources:
             x = _c64(s["pos"])
-            check(self.ctx, L.hrt_add_point_source(self.ctx, _ptr(x), float(s["L"]), float(s["Teff"])))
+            if "spectrum" in s:                 # its own f_nu: (nu, f_nu)
+                snu, sf = _c64(s["spectrum"][0]), _c64(s["spectrum"][1])
+                check(self.ctx, L.hrt_add_point_source_spectrum(self.ctx, _ptr(x), float(s["L"]), len(snu), _ptr(snu),
+                                                                _ptr(sf)))
+            else:
+                check(self.ctx, L.hrt_add_point_source(self.ctx, _ptr(x), float(s["L"]), float(s["Teff"])))
         for e in getattr(wl, "external_sources", []) or []:
             c = _c64(e["center"])
             check(self.ctx, L.hrt_add_external_source(self.ctx, _ptr(c), float(e["radius"]), float(e["L"]),

@@ -56,7 +56,8 @@ class Workload:
     albedo: np.ndarray                  # single-scattering albedo at nu
     g: float                            # Henyey-Greenstein asymmetry parameter
     T_nodes: np.ndarray                 # temperature nodes of the emissivity / Planck-mean table (K)
-    sources: list = field(default_factory=list)   # dicts: pos (cm, 3), L (erg/s), Teff (K)
+    sources: list = field(default_factory=list)   # dicts: pos (cm, 3), L (erg/s), Teff (K) or a
+                                        # spectrum of its own, "spectrum": (nu Hz, f_nu any scale)
     cell_source: dict | None = None     # {"L": float64 [Nc] erg/s, "Teff": K}
     external_sources: list = field(default_factory=list)  # dicts: center (cm, 3), radius (cm), L, Teff
     obs_incl: np.ndarray = field(default_factory=lambda: np.zeros(0))  # rad

@@ -1,0 +1,138 @@
+"""The remaining setup and read-out calls of the C ABI on the GPU: point sources with a spectrum
+of their own (against the oracle's table of it, step by step and over a whole iteration), the
+model id that keys the random streams, clearing and re-adding sources, the library stream, the
+device read-out of the SEDs and the watchdog report."""
+import numpy as np
+import pytest
+
+from oracle import mc as M
+from paper_1112_1071_gb300 import hrt
+from paper_1112_1071_gb300 import workloads as W
+from tests.gpu_helpers import dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+NU = W.dust_table()[0]
+
+
+def _own_spectrum_sphere(n_packets=50_000):
+    """The tiny sphere with its star given a spectrum of its own: a broken power law that is
+    zero over part of the band (exercising the log-log pieces, a zero node and the range ends)."""
+    wl = W.tiny_sphere(n_packets=n_packets)
+    unu = np.array([NU[10] * 1.01, NU[30], NU[55], NU[70], NU[95] * 0.99])
+    f = np.array([1.0, 40.0, 0.0, 5.0, 0.3])
+    wl.sources = [dict(pos=s["pos"], L=s["L"], spectrum=(unu, f)) for s in wl.sources]
+    return wl
+
+
+def test_own_spectrum_frequencies_match_oracle():
+    torch = torch_cuda()
+    wl = _own_spectrum_sphere()
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    rng = np.random.default_rng(9)
+    n = 50000
+    us = ((rng.integers(0, 2 ** 24, n) + 1) * 2.0 ** -24).astype(np.float32)
+    ud, sd = dev(us), dev(np.zeros(n, np.int32))
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    m.step("hrt_step_sample_source", n, sd.data_ptr(), ud.data_ptr(), out.data_ptr())
+    got = out.cpu().numpy()
+    want = np.array([M.sample_table(om.spec_nu, om.spec_cdf[0], float(us[q])) for q in range(n)])
+    rel = np.abs(got - want) / want
+    assert (rel > 1e-5).mean() < 1e-3 and np.median(rel) < 1e-6
+    # nothing is drawn beyond the source-grid intervals that hold the spectrum's end nodes
+    unu = wl.sources[0]["spectrum"][0]
+    lo = om.spec_nu[np.searchsorted(om.spec_nu, unu[0]) - 1]
+    hi = om.spec_nu[np.searchsorted(om.spec_nu, unu[-1])]
+    assert got.min() >= lo * (1 - 1e-6) and got.max() <= hi * (1 + 1e-6)
+
+
+def _lockstep(st, m, om, ref):
+    assert st["e_escaped"] + st["e_killed"] == pytest.approx(om.L_tot, rel=1e-12)
+    acc = m.absorbed()
+    seen = ref["acc"] > 0
+    rel = np.abs(acc[seen] - ref["acc"][seen]) / ref["acc"][seen]
+    assert np.median(rel) < 1e-4, np.median(rel)
+    assert st["n_crossings"] == pytest.approx(ref["n_crossings"], rel=2e-3)
+
+
+def test_own_spectrum_iteration_matches_oracle():
+    wl = _own_spectrum_sphere()
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    for _ in range(2):
+        st = m.run_iteration()
+        ref = om.run_iteration(nthreads=16)
+        _lockstep(st, m, om, ref)
+
+
+def test_model_id_keys_the_streams():
+    wl = W.tiny_sphere(n_packets=50_000)
+    om = M.OracleModel(wl)
+    om.model_key = 7
+    m = hrt.Model(wl)
+    hrt.check(m.ctx, hrt.load().hrt_set_model_id(m.ctx, 7))
+    st = m.run_iteration()
+    ref = om.run_iteration(nthreads=16)
+    _lockstep(st, m, om, ref)
+    # other streams: the same model with id 0 deposits differently
+    m0 = hrt.Model(wl)
+    m0.run_iteration()
+    seen = ref["acc"] > 0
+    assert np.median(np.abs(m0.absorbed()[seen] / ref["acc"][seen] - 1)) > 1e-3
+
+
+def test_clearing_and_re_adding_sources_gives_the_same_model():
+    wl = W.tiny_sphere(n_packets=50_000)
+    fresh = hrt.Model(wl)
+    st0 = fresh.run_iteration()
+    m = hrt.Model(wl)
+    L = hrt.load()
+    hrt.check(m.ctx, L.hrt_clear_sources(m.ctx))
+    with pytest.raises(hrt.HrtError):
+        m.run_iteration()                          # no sources
+    for s in wl.sources:
+        x = np.asarray(s["pos"], np.float64)
+        hrt.check(m.ctx, L.hrt_add_point_source(m.ctx, x.ctypes.data, float(s["L"]), float(s["Teff"])))
+    st = m.run_iteration()
+    assert st["n_crossings"] == st0["n_crossings"] and st["n_interactions"] == st0["n_interactions"]
+    np.testing.assert_allclose(m.absorbed(), fresh.absorbed(), rtol=1e-10)
+    np.testing.assert_allclose(m.temperature(), fresh.temperature(), rtol=1e-10)
+
+
+def test_library_stream_and_device_read_out():
+    torch = torch_cuda()
+    wl = W.tiny_sphere(n_packets=50_000)
+    ref = hrt.Model(wl)
+    ref.run_iteration()
+    ref.run_iteration(peel=1, update_temperature=0)
+    s = torch.cuda.Stream()
+    m = hrt.Model(wl)
+    hrt.check(m.ctx, hrt.load().hrt_set_stream(m.ctx, s.cuda_stream))
+    m.run_iteration()
+    st = m.run_iteration(peel=1, update_temperature=0)
+    assert st["n_peel_crossings"] > 0
+    np.testing.assert_allclose(m.sed(), ref.sed(), rtol=1e-10)
+    d = torch.zeros(m.nobs * wl.nsed, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()                        # the fill runs on torch's stream, the read-out on s
+    hrt.check(m.ctx, hrt.load().hrt_get_sed_device(m.ctx, d.data_ptr(), d.numel()))
+    s.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy().reshape(m.nobs, wl.nsed), m.sed())
+    assert hrt.load().hrt_get_sed_device(m.ctx, d.data_ptr(), d.numel() - 1) == hrt.HRT_EINVAL
+
+
+def test_watchdog_report_after_a_timeout():
+    wl = W.flared_disk(n_packets=2_000_000, n_r=100, n_theta=64)
+    m = hrt.Model(wl)
+    L = hrt.load()
+    buf = np.zeros(512, np.float32)
+    assert L.hrt_get_watchdog_report(m.ctx, buf.ctypes.data, 511) == hrt.HRT_EINVAL
+    with pytest.raises(hrt.HrtError) as e:
+        m.run_iteration(params=hrt.default_params(watchdog_ms=0.05))
+    assert e.value.code == hrt.HRT_ETIMEDOUT
+    r = L.hrt_get_watchdog_report(m.ctx, buf.ctypes.data, 512)
+    assert 0 <= r <= 32
+    rec = buf.reshape(32, 16)[:r]
+    assert np.all(rec[:, 0] == np.rint(rec[:, 0])) and np.all((rec[:, 0] >= 0) & (rec[:, 0] < 16))  # lane modes
+    st = m.run_iteration(n_packets=10_000)                      # and the context still works
+    assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
