@@ -111,8 +111,12 @@ int hrt_add_point_source(hrt_ctx* ctx, const double x[3], double L, double Teff)
  * at emission (background).  L, R, Teff > 0, c finite; HRT_ESTATE before a grid is set. */
 int hrt_add_external_source(hrt_ctx* ctx, const double c[3], double radius, double L, double Teff);
 
-/* Point source with a user spectrum f_nu on n strictly increasing frequencies (any positive
- * normalisation; the part inside the dust band carries all of L). */
+/* Point source (Sect. 2.1.1) at x[3] with luminosity L and a spectrum of its own: f_nu (>= 0,
+ * any normalisation) at n >= 2 strictly increasing frequencies nu (Hz).  Between two nodes f_nu
+ * is interpolated as a power law (log-log), linearly where either value is zero, and it is zero
+ * outside the nodes; it is tabulated on the 1000 log-spaced frequencies of the source grid over
+ * the dust band, and the in-band part carries all of L.  HRT_EINVAL for a non-finite or negative
+ * value or non-increasing frequencies; the other checks are those of hrt_add_point_source. */
 int hrt_add_point_source_spectrum(hrt_ctx* ctx, const double x[3], double L, int n,
                                   const double* nu, const double* fnu);
 
