@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "nn.h"
@@ -198,7 +199,10 @@ static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, 
     // the attribute belongs to the current device's context: set it on every launch
     cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    static int smem = 0;
+    // residency-capped size, computed once per instantiation (host threads may race to fill it
+    // with the same value)
+    static std::atomic<int> smem_cached{0};
+    int smem = smem_cached.load(std::memory_order_relaxed);
     if (smem == 0) {
         int bytes = smem_bytes<BN>();
         for (;;) {
@@ -210,6 +214,7 @@ static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, 
             if (bytes > 200 * 1024) return cudaErrorInvalidConfiguration;
         }
         smem = bytes;
+        smem_cached.store(bytes, std::memory_order_relaxed);
     }
     const unsigned bricks = (unsigned)(((W + BRICK_X - 1) / BRICK_X) * ((H + BRICK_Y - 1) / BRICK_Y) * D);
     const dim3 grid(bricks, (unsigned)(Cout / BN), (unsigned)N);
@@ -372,7 +377,8 @@ static cudaError_t launch_wgrad_tc(const bf16* in, const bf16* dy, float* dw, in
     constexpr int MAX_RESIDENT = 512 / NCOLS;
     cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    static int smem = 0;
+    static std::atomic<int> smem_cached{0};
+    int smem = smem_cached.load(std::memory_order_relaxed);
     if (smem == 0) {
         int bytes = 2 * (128 + BN) * WG_KV * 2 + 32;
         for (;;) {
@@ -384,6 +390,7 @@ static cudaError_t launch_wgrad_tc(const bf16* in, const bf16* dy, float* dw, in
             if (bytes > 200 * 1024) return cudaErrorInvalidConfiguration;
         }
         smem = bytes;
+        smem_cached.store(bytes, std::memory_order_relaxed);
     }
     const int TPG = 128 / CB;
     const int blocks_mn = ((27 + TPG - 1) / TPG) * (Cin / CB) * (Cout / BN);
