@@ -136,3 +136,19 @@ def test_watchdog_report_after_a_timeout():
     assert np.all(rec[:, 0] == np.rint(rec[:, 0])) and np.all((rec[:, 0] >= 0) & (rec[:, 0] < 16))  # lane modes
     st = m.run_iteration(n_packets=10_000)                      # and the context still works
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
+
+
+def test_escape_bins_match_oracle():
+    """The escape tally by direction cosine and wavelength (Sect. 2.6.1), same packets as the
+    oracle's: bin totals within what the few packets that part from lockstep can move."""
+    wl = W.tiny_sphere(n_packets=50_000)
+    om = M.OracleModel(wl)
+    m = hrt.Model(wl)
+    m.run_iteration()
+    ref = om.run_iteration(nthreads=16)
+    esc, resc = m.escape(), ref["esc"]
+    assert esc.sum() == pytest.approx(resc.sum(), rel=1e-3)
+    np.testing.assert_allclose(esc.sum(axis=1), resc.sum(axis=1), rtol=1e-2)
+    lam, rlam = esc.sum(axis=0), resc.sum(axis=0)
+    big = rlam > 1e-2 * rlam.max()
+    np.testing.assert_allclose(lam[big], rlam[big], rtol=2e-2)
