@@ -77,3 +77,95 @@ def test_isrf_cloud_encloses_the_grid_and_has_its_optical_depth(grid):
     (e,) = wl.external_sources
     far = {"cartesian": math.sqrt(3) * h, "spherical": h, "cylindrical": math.sqrt(2) * h}[grid]
     assert e["radius"] > far
+
+
+def test_tiny_sphere_recipe():
+    wl = W.tiny_sphere()
+    rho = np.asarray(wl.rho, dtype=np.float64)
+    assert rho.shape == (32, 32, 32)
+    w = np.asarray(wl.walls[0])
+    assert w[0] == pytest.approx(-100 * W.AU) and w[-1] == pytest.approx(100 * W.AU) and w[16] == 0.0
+    c = 0.5 * (w[1:] + w[:-1])
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    inside = np.sqrt(xx ** 2 + yy ** 2 + zz ** 2) < 80 * W.AU
+    assert np.all(rho[~inside] == 0) and np.all(rho[inside] == rho[inside].flat[0])
+    # radial optical depth at 1 micron of the continuous sphere is 1
+    assert rho[inside].flat[0] * W.chi_at_lambda_um(1.0) * 80 * W.AU == pytest.approx(1.0, rel=1e-6)
+    assert wl.sources == [dict(pos=(0.0, 0.0, 0.0), L=W.LSUN, Teff=5800.0)]
+    np.testing.assert_allclose(np.degrees(wl.obs_incl), [12.5, 42.5, 77.5])
+
+
+def test_flared_disk_recipe():
+    wl = W.flared_disk()
+    rho = np.asarray(wl.rho, dtype=np.float64)
+    assert rho.shape == (1, 128, 200)
+    rw, tw = np.asarray(wl.walls[0]), np.asarray(wl.walls[1])
+    assert rw[0] == pytest.approx(W.AU) and rw[-1] == pytest.approx(1000 * W.AU)
+    q = rw[1:] / rw[:-1]
+    np.testing.assert_allclose(q, q[0], rtol=1e-9)                        # log-spaced radii
+    dth = np.diff(tw)
+    assert tw[0] == 0.0 and tw[-1] == pytest.approx(math.pi) and tw[64] == pytest.approx(math.pi / 2)
+    assert dth.argmin() in (63, 64) and dth[0] / dth[63] > 50              # cones crowd the midplane
+    np.testing.assert_allclose(dth, dth[::-1], rtol=1e-9)
+    np.testing.assert_allclose(rho[0], rho[0, ::-1], rtol=1e-5)            # mirror symmetric
+    # midplane radial tau_550 of 100 (the cells next to the midplane are far thinner than h)
+    tau = float(np.sum(0.5 * (rho[0, 63] + rho[0, 64]) * np.diff(rw)) * W.chi_at_lambda_um(0.55))
+    assert tau == pytest.approx(100.0, rel=2e-3)
+    # vertical profile at 100 AU: Gaussian in z with h = 10 AU
+    i = int(np.argmin(np.abs(0.5 * (rw[1:] + rw[:-1]) - 100 * W.AU)))
+    rc = 0.5 * (rw[i] + rw[i + 1])
+    thc = 0.5 * (tw[1:] + tw[:-1])
+    z, R = rc * np.cos(thc), rc * np.sin(thc)
+    h = 10 * W.AU * (R / (100 * W.AU)) ** 1.125
+    col = rho[0, :, i] * (R / (100 * W.AU))                                # remove the 1/R factor
+    near = np.abs(z) < 3 * h
+    np.testing.assert_allclose(col[near] / np.exp(-0.5 * (z[near] / h[near]) ** 2), col[64] / math.exp(
+        -0.5 * (z[64] / h[64]) ** 2), rtol=1e-5)
+    assert len(wl.obs_incl) == 10 and wl.nsed == 250
+    np.testing.assert_allclose(np.cos(wl.obs_incl), 0.05 + 0.1 * np.arange(10))
+
+
+def test_batched_disk_parameters_span_their_ranges():
+    models = W.batched_disks(size_scale=0.1)
+    assert len(models) == 512
+    r_in = np.array([m.walls[0][0] for m in models]) / W.AU
+    teff = np.array([m.sources[0]["Teff"] for m in models])
+    npk = np.array([m.n_packets for m in models])
+    assert r_in.min() >= 0.1 and r_in.max() <= 5.0 and teff.min() >= 3000 and teff.max() <= 10000
+    assert npk.min() >= 1e5 and npk.max() <= 1e7
+    # log-uniform packet budgets and inner radii, uniform temperatures
+    from scipy import stats
+    assert stats.kstest(np.log10(npk), stats.uniform(5, 2).cdf).pvalue > 1e-3
+    assert stats.kstest(np.log10(r_in), stats.uniform(-1, math.log10(50)).cdf).pvalue > 1e-3
+    assert stats.kstest(teff, stats.uniform(3000, 7000).cdf).pvalue > 1e-3
+    assert len({m.walls[0].size for m in models}) > 5                       # uneven grids
+
+
+def test_turbulent_cloud_recipe():
+    wl = W.turbulent_cloud(n=64, n_packets=1000)
+    rho = np.asarray(wl.rho, dtype=np.float64)
+    side = 0.65 * W.PC
+    assert rho.shape == (64, 64, 64)
+    assert rho.mean() * W.chi_at_lambda_um(0.55) * side == pytest.approx(10.0, rel=1e-5)
+    lnr = np.log(rho)
+    assert lnr.std() == pytest.approx(1.5, rel=1e-4)
+    # the log density's power spectrum falls as k^(-11/3)
+    P = np.abs(np.fft.rfftn(lnr - lnr.mean())) ** 2
+    kx, ky, kz = np.fft.fftfreq(64)[:, None, None], np.fft.fftfreq(64)[None, :, None], np.fft.rfftfreq(64)[None, None, :]
+    k = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    kb = np.geomspace(3 / 64, 0.4, 10)
+    mids, power = [], []
+    for a, b in zip(kb[:-1], kb[1:]):
+        sel = (k >= a) & (k < b)
+        mids.append(math.sqrt(a * b))
+        power.append(P[sel].mean())
+    slope = np.polyfit(np.log(mids), np.log(power), 1)[0]
+    assert slope == pytest.approx(-11 / 3, abs=0.25)
+    assert len(wl.sources) == 20
+    pos = np.array([s["pos"] for s in wl.sources])
+    assert np.all(np.abs(pos) < side / 2)
+    T = np.array([s["Teff"] for s in wl.sources])
+    L = np.array([s["L"] for s in wl.sources]) / W.LSUN
+    assert T.min() >= 3000 and T.max() <= 20000 and L.min() >= 0.1 and L.max() <= 100
+    np.testing.assert_allclose(np.degrees([wl.obs_incl[0], wl.obs_az[0]]), [45.0, 45.0])
+    np.testing.assert_allclose(wl.img_lam_um, [1.25, 3.6, 8.0, 70.0, 250.0, 500.0])
