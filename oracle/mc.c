@@ -7,6 +7,12 @@
  * load it.
  *
  * What it follows:
+ *   Sect. 2.1.1  sources: point sources (a blackbody of Teff or a spectrum of their own, both
+ *              tabulated by the caller), a diffuse source whose cells emit in proportion to
+ *              their luminosity from points uniform in their volume, external isotropic
+ *              fields emitted inwards from an enclosing sphere.
+ *   Sect. 2.1.2  grids: Cartesian, spherical-polar (with an empty inner hole) and
+ *              cylindrical-polar (with an empty inner cylinder), walls given by the caller.
  *   Sect. 2.2  packet life: emission by source luminosity PDF, tau = -ln(zeta), propagation
  *              to the sampled optical depth or escape, absorb if zeta > albedo else scatter,
  *              new tau after every interaction.

@@ -11,6 +11,11 @@ baseline of the bench use it.  It shares no code with the CUDA library.
   Adot = E(T) = 4 pi int kappa_nu B_nu(T) dnu, inverted on the tabulated E.
 * Sect. 2.4, Eqs. 4-6: delta(x1, x2) = max(x1/x2, x2/x1); R_j = delta over cells; the
   p-th percentile Q and its change Delta.
+* Sect. 2.1.1: source spectra on a log-spaced grid over the dust band (a blackbody of Teff, or
+  the source's own f_nu interpolated log-log between its nodes), renormalised so that the
+  in-band part carries all of the luminosity.
+* App. A and Sect. 2.2 (modified random walk): Rosseland means of the extinction and of the
+  transport extinction, and the Planck-mean absorption coefficient, on the temperature nodes.
 """
 from __future__ import annotations
 
