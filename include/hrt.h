@@ -116,7 +116,9 @@ int hrt_add_external_source(hrt_ctx* ctx, const double c[3], double radius, doub
  * is interpolated as a power law (log-log), linearly where either value is zero, and it is zero
  * outside the nodes; it is tabulated on the 1000 log-spaced frequencies of the source grid over
  * the dust band, and the in-band part carries all of L.  HRT_EINVAL for a non-finite or negative
- * value or non-increasing frequencies; the other checks are those of hrt_add_point_source. */
+ * value or non-increasing frequencies; the other checks are those of hrt_add_point_source.  A
+ * spectrum with no flux at any frequency of that grid has nothing to carry L: the next
+ * hrt_run_iteration returns HRT_EINVAL. */
 int hrt_add_point_source_spectrum(hrt_ctx* ctx, const double x[3], double L, int n,
                                   const double* nu, const double* fnu);
 

@@ -19,6 +19,7 @@
 using namespace hrt;
 
 #include "ctx_internal.h"
+#include "user_spectrum.h"
 
 
 namespace {
@@ -240,6 +241,18 @@ int stage_dust(hrt_ctx* ctx) {
 
 int stage_sources(hrt_ctx* ctx) {
     const cudaStream_t s = ctx->stream;
+    // spectrum grid: NSPEC log-spaced frequencies over the dust band
+    std::vector<double> snu(NSPEC);
+    const double a = ctx->nu.front(), b = ctx->nu.back();
+    for (int k = 0; k < NSPEC; ++k) snu[k] = a * std::pow(b / a, (double)k / (NSPEC - 1));
+    snu.front() = a;
+    snu.back() = b;
+    // a spectrum of a source's own must have flux in the band to carry the source's L
+    for (size_t i = 0; i < ctx->pts.size(); ++i) {
+        const PointSrc& p = ctx->pts[i];
+        if (!p.unu.empty() && !user_spectrum_has_flux(snu.data(), NSPEC, p.unu.data(), p.uf.data(), (int)p.unu.size()))
+            return ctx->fail(HRT_EINVAL, "source %zu: its spectrum has no flux in the dust band", i);
+    }
     const int npt = (int)ctx->pts.size();
     const int next = (int)ctx->ext.size();
     const bool cell = !ctx->Lcell.empty();
@@ -283,12 +296,6 @@ int stage_sources(hrt_ctx* ctx) {
     ctx->L_tot = cum;
     for (auto& v : cdf) v /= cum;
     cdf.back() = 1.0;
-    // spectrum grid: NSPEC log-spaced frequencies over the dust band
-    std::vector<double> snu(NSPEC);
-    const double a = ctx->nu.front(), b = ctx->nu.back();
-    for (int k = 0; k < NSPEC; ++k) snu[k] = a * std::pow(b / a, (double)k / (NSPEC - 1));
-    snu.front() = a;
-    snu.back() = b;
     std::vector<float> snuf(snu.begin(), snu.end());
     if (unu.empty()) { unu.push_back(0.0); uf.push_back(0.0); }
     CK(ctx->d_src_pos.upload(pos.data(), pos.size(), s), "sources");

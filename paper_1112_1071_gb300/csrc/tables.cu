@@ -9,6 +9,7 @@
 
 #include "hrt_internal.h"
 #include "planck.cuh"
+#include "user_spectrum.h"
 
 namespace hrt {
 
@@ -46,19 +47,6 @@ cudaError_t launch_emission_tables(int nnu, const double* nu, const double* kapp
                                    double* lnE, float* cdf, cudaStream_t s) {
     k_emission_tables<<<(nT + 127) / 128, 128, 0, s>>>(nnu, nu, kappa, nT, T, E, lnE, cdf);
     return cudaGetLastError();
-}
-
-// User spectrum f_nu on its own nodes, interpolated log-log onto the source grid (0 outside).
-__device__ __forceinline__ double user_spectrum(double v, const double* x, const double* f, int n) {
-    if (v < x[0] || v > x[n - 1]) return 0.0;
-    int lo = 0, hi = n - 1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (x[mid] <= v) lo = mid; else hi = mid;
-    }
-    if (f[lo] <= 0.0 || f[lo + 1] <= 0.0) return f[lo] + (f[lo + 1] - f[lo]) * (v - x[lo]) / (x[lo + 1] - x[lo]);
-    const double t = log(v / x[lo]) / log(x[lo + 1] / x[lo]);
-    return exp((1.0 - t) * log(f[lo]) + t * log(f[lo + 1]));
 }
 
 // one block per source: the cumulative trapezoid of the spectrum on the source grid,

@@ -152,3 +152,13 @@ def test_escape_bins_match_oracle():
     lam, rlam = esc.sum(axis=0), resc.sum(axis=0)
     big = rlam > 1e-2 * rlam.max()
     np.testing.assert_allclose(lam[big], rlam[big], rtol=2e-2)
+
+
+def test_spectrum_without_flux_in_the_band_is_rejected():
+    wl = W.tiny_sphere(n_packets=1000)
+    wl.sources = [dict(pos=(0.0, 0.0, 0.0), L=W.LSUN, spectrum=(np.array([NU[-1] * 2, NU[-1] * 3]), np.ones(2)))]
+    m = hrt.Model(wl)
+    with pytest.raises(hrt.HrtError) as e:
+        m.run_iteration()
+    assert e.value.code == hrt.HRT_EINVAL
+    assert "no flux" in hrt.load().hrt_last_error(m.ctx).decode()
