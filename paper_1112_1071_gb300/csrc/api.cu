@@ -565,6 +565,9 @@ static int add_point(hrt_ctx* ctx, const double x[3], double L, double teff, int
     if (ctx->gtype == GRID_CARTESIAN) {
         for (int a = 0; a < 3; ++a)
             if (x[a] < ctx->w[a].front() || x[a] > ctx->w[a].back()) return ctx->fail(HRT_EINVAL, "source outside the grid");
+    } else if (ctx->gtype == GRID_CYLINDRICAL) {       // inside the outer cylinder, between the end planes
+        if (std::hypot(x[0], x[1]) >= ctx->w[0].back() || x[2] < ctx->w[1].front() || x[2] > ctx->w[1].back())
+            return ctx->fail(HRT_EINVAL, "source outside the grid");
     } else if (std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) >= ctx->w[0].back()) {
         return ctx->fail(HRT_EINVAL, "source outside the grid");
     }
@@ -573,13 +576,14 @@ static int add_point(hrt_ctx* ctx, const double x[3], double L, double teff, int
     p.L = L;
     p.teff = teff;
     if (n > 0) {
-        if (!nu || !f || n < 2 || !increasing(nu, n) || !finite_all(f, n)) return ctx->fail(HRT_EINVAL, "source spectrum");
+        if (!nu || !f || n < 2 || !finite_all(nu, n) || !increasing(nu, n) || !(nu[0] > 0) || !finite_all(f, n))
+            return ctx->fail(HRT_EINVAL, "source spectrum: frequencies must be finite, > 0 and increasing");
         for (int k = 0; k < n; ++k)
             if (f[k] < 0) return ctx->fail(HRT_EINVAL, "source spectrum negative");
         p.unu.assign(nu, nu + n);
         p.uf.assign(f, f + n);
-    } else if (!(teff > 0)) {
-        return ctx->fail(HRT_EINVAL, "source: Teff must be > 0");
+    } else if (!(teff > 0) || !std::isfinite(teff)) {
+        return ctx->fail(HRT_EINVAL, "source: Teff must be finite and > 0");
     }
     ctx->pts.push_back(p);
     ctx->dirty_src = true;

@@ -162,3 +162,25 @@ def test_spectrum_without_flux_in_the_band_is_rejected():
         m.run_iteration()
     assert e.value.code == hrt.HRT_EINVAL
     assert "no flux" in hrt.load().hrt_last_error(m.ctx).decode()
+
+
+def test_point_source_checks():
+    wl = W.cylindrical_disk(n_R=20, n_z=16, n_packets=1000)
+    m = hrt.Model(wl)
+    L = hrt.load()
+    R_out, z_lo, z_hi = wl.walls[0][-1], wl.walls[1][0], wl.walls[1][-1]
+    add = lambda x, Teff=5000.0: L.hrt_add_point_source(m.ctx, np.asarray(x, np.float64).ctypes.data, W.LSUN, Teff)
+    # inside the cylinder although farther than R_out from the origin
+    assert add([0.97 * R_out, 0.0, 0.9 * z_hi]) == hrt.HRT_OK
+    assert add([0.0, 0.0, 1.1 * z_hi]) == hrt.HRT_EINVAL          # beyond an end plane
+    assert add([0.0, 0.0, 1.1 * z_lo]) == hrt.HRT_EINVAL
+    assert add([0.8 * R_out, 0.8 * R_out, 0.0]) == hrt.HRT_EINVAL  # outside the outer cylinder
+    assert add([0.0, 0.0, 0.0], Teff=float("inf")) == hrt.HRT_EINVAL
+    x = np.zeros(3)
+    for nu in ([0.0, 1e14], [-1e14, 1e14], [1e14, float("nan")], [2e14, 1e14]):
+        nu = np.asarray(nu, np.float64)
+        f = np.ones(2)
+        assert L.hrt_add_point_source_spectrum(m.ctx, x.ctypes.data, W.LSUN, 2, nu.ctypes.data,
+                                               f.ctypes.data) == hrt.HRT_EINVAL
+    st = m.run_iteration()                                          # the accepted sources run
+    assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
