@@ -647,9 +647,16 @@ int hrt_set_peeloff(hrt_ctx* ctx, int nobs, const double* incl, const double* az
                     double lam_max_um, int img_nx, int img_ny, double img_half_extent_cm, int nimg, const double* img_lam_um) {
     if (!ctx) return HRT_EINVAL;
     if (nobs < 0 || (nobs > 0 && (!incl || !az))) return ctx->fail(HRT_EINVAL, "peeloff: observers");
-    if (nsed < 1 || !(lam_min_um > 0) || !(lam_max_um > lam_min_um)) return ctx->fail(HRT_EINVAL, "peeloff: SED bins");
-    if (img_nx < 0 || img_ny < 0 || (img_nx > 0 && (img_ny < 1 || !(img_half_extent_cm > 0) || nimg < 1 || !img_lam_um)))
+    if (nsed < 1 || !(lam_min_um > 0) || !(lam_max_um > lam_min_um) || !std::isfinite(lam_max_um))
+        return ctx->fail(HRT_EINVAL, "peeloff: SED bins");
+    if (img_nx < 0 || img_ny < 0 ||
+        (img_nx > 0 && (img_ny < 1 || !(img_half_extent_cm > 0) || !std::isfinite(img_half_extent_cm) || nimg < 1 ||
+                        !img_lam_um)))
         return ctx->fail(HRT_EINVAL, "peeloff: image");
+    if (img_nx > 0)
+        for (int l = 0; l < nimg; ++l)
+            if (!(img_lam_um[l] > 0) || !std::isfinite(img_lam_um[l]))
+                return ctx->fail(HRT_EINVAL, "peeloff: image wavelength %d must be finite and > 0", l);
     if (nobs > 0 && (!finite_all(incl, nobs) || !finite_all(az, nobs))) return ctx->fail(HRT_EINVAL, "peeloff: angles");
     ctx->nobs = nobs;
     ctx->incl.assign(incl, incl + nobs);

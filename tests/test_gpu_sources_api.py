@@ -184,3 +184,25 @@ def test_point_source_checks():
                                                f.ctypes.data) == hrt.HRT_EINVAL
     st = m.run_iteration()                                          # the accepted sources run
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
+
+
+def test_peeloff_checks():
+    wl = W.tiny_sphere(n_packets=1000)
+    m = hrt.Model(wl)
+    L = hrt.load()
+    inc, az = np.array([0.3]), np.array([0.0])
+    lam = np.array([1.0, -2.0])
+    inf = float("inf")
+
+    def peel(nsed=10, lo=0.1, hi=1000.0, nx=0, half=1e15, lam=lam, nimg=1):
+        return L.hrt_set_peeloff(m.ctx, 1, inc.ctypes.data, az.ctypes.data, nsed, lo, hi, nx, nx, half, nimg,
+                                 lam.ctypes.data)
+
+    assert peel() == hrt.HRT_OK
+    assert peel(nx=4) == hrt.HRT_OK
+    for bad in (dict(nsed=0), dict(lo=0.0), dict(hi=0.05), dict(hi=inf), dict(nx=4, half=inf), dict(nx=4, half=0.0),
+                dict(nx=4, nimg=2), dict(nx=4, nimg=0)):
+        assert peel(**bad) == hrt.HRT_EINVAL, bad
+    assert peel() == hrt.HRT_OK
+    st = m.run_iteration(peel=1, update_temperature=0)
+    assert st["n_peel_crossings"] > 0
