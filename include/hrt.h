@@ -152,8 +152,9 @@ typedef struct {
     double q_thres;              /* Q threshold (e.g. 1.02 on T, 2 on Adot) */
     double delta_thres;          /* Delta threshold (INFINITY disables the Delta test) */
     int32_t kernel;              /* hrt_kernel */
-    int32_t block_size;          /* threads per block, 0 = tuned default */
-    int32_t blocks_per_sm;       /* persistent blocks per SM, 0 = tuned default */
+    int32_t block_size;          /* threads per block: 0 or 256 (the propagation kernels are compiled
+                                    for 256-thread blocks) */
+    int32_t blocks_per_sm;       /* persistent blocks per SM, 0 = tuned default (>= 0) */
     int32_t regroup_threshold;   /* event kernel: a warp leaves the walk phase when fewer lanes
                                     than this are still walking (1..32, 0 = tuned default) */
     double watchdog_ms;          /* > 0: the propagation kernel stops after this long and the call

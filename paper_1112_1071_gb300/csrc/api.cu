@@ -748,6 +748,14 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (!(P.mrw_gamma >= 0) || !std::isfinite(P.mrw_gamma))
         return ctx->fail(HRT_EINVAL, "mrw_gamma must be finite and >= 0");
     if (P.peel_queue_events < 0) return ctx->fail(HRT_EINVAL, "peel_queue_events must be >= 0");
+    if (P.kernel != HRT_KERNEL_EVENT && P.kernel != HRT_KERNEL_PLAIN) return ctx->fail(HRT_EINVAL, "unknown kernel");
+    if (P.quantity != 0 && P.quantity != 1) return ctx->fail(HRT_EINVAL, "quantity must be 0 (T) or 1 (Adot)");
+    if (P.block_size != 0 && P.block_size != 256)
+        return ctx->fail(HRT_EINVAL, "block_size must be 0 or 256 (the kernels are compiled for 256 threads)");
+    if (P.blocks_per_sm < 0 || P.regroup_threshold < 0 || P.regroup_threshold > 32)
+        return ctx->fail(HRT_EINVAL, "blocks_per_sm >= 0 and regroup_threshold in [0, 32] required");
+    if (!(P.watchdog_ms >= 0) || !std::isfinite(P.watchdog_ms)) return ctx->fail(HRT_EINVAL, "watchdog_ms must be finite and >= 0");
+    if (std::isnan(P.q_thres) || std::isnan(P.delta_thres)) return ctx->fail(HRT_EINVAL, "convergence thresholds are NaN");
     const int64_t n_total = P.n_total > 0 ? P.n_total : n_packets;
     if (P.first_packet < 0 || P.n_total < 0 || n_total > 0x100000000ll || P.first_packet + n_packets > n_total)
         return ctx->fail(HRT_EINVAL, "packet share: need 0 <= first_packet, first_packet + n_packets <= n_total <= 2^32");

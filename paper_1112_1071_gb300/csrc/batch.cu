@@ -334,8 +334,13 @@ int hrt_batch_tune(hrt_batch* b, const int64_t* n_packets) {
     const double scale = total > ((int64_t)1 << 24) ? (double)((int64_t)1 << 24) / (double)total : 1.0;
     std::vector<int64_t> trial(b->models.size());
     for (size_t m = 0; m < trial.size(); ++m) trial[m] = std::max<int64_t>(1, (int64_t)(n_packets[m] * scale));
+    // the caller's device comes back on every exit
+    auto done = [&](int code) {
+        if (prev >= 0) cudaSetDevice(prev);
+        return code;
+    };
     int rc = build_batch(b, trial.data(), P);
-    if (rc != HRT_OK) return rc;
+    if (rc != HRT_OK) return done(rc);
     const int regroups[] = {12, 16, 20, 24};
     const int per_sm[] = {2, 3};
     float best = 1e30f;
@@ -347,9 +352,9 @@ int hrt_batch_tune(hrt_batch* b, const int64_t* n_packets) {
             for (int rep = 0; rep < 2; ++rep) {     // first run warms up
                 cudaEventRecord(b->ev0, b->stream);
                 rc = enqueue_iteration(b, P, true);
-                if (rc != HRT_OK) return rc;
+                if (rc != HRT_OK) return done(rc);
                 cudaEventRecord(b->ev1, b->stream);
-                if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(cudaGetLastError());
+                if (cudaStreamSynchronize(b->stream) != cudaSuccess) return done(bfail(cudaGetLastError()));
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, b->ev0, b->ev1);
                 if (rep == 1 && ms < best) {
@@ -377,6 +382,10 @@ int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hr
     if (params) P = *params;
     else hrt_default_params(&P);
     if (!(P.p > 0 && P.p <= 1) || P.max_interactions < 0) return HRT_EINVAL;
+    if ((P.quantity != 0 && P.quantity != 1) || (P.block_size != 0 && P.block_size != 256) || P.blocks_per_sm < 0 ||
+        P.regroup_threshold < 0 || P.regroup_threshold > 32 || !(P.watchdog_ms >= 0) || !std::isfinite(P.watchdog_ms) ||
+        std::isnan(P.q_thres) || std::isnan(P.delta_thres))
+        return HRT_EINVAL;
     // Lucy iterations only: the extensions and imaging passes run in single-model calls
     if (P.mrw_gamma != 0 || P.pda_min_visits != 0 || P.raytrace_rays != 0 || P.peel != 0 || !P.update_temperature)
         return HRT_EINVAL;
@@ -389,7 +398,10 @@ int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hr
     int rc = HRT_OK;
     if (rebuild) {
         rc = build_batch(b, n_packets, P);
-        if (rc != HRT_OK) return rc;
+        if (rc != HRT_OK) {
+            if (prev >= 0) cudaSetDevice(prev);
+            return rc;
+        }
     } else {
         // restart the convergence state from the contexts (a new run of the batch)
         std::vector<BatchState> st(n);
@@ -406,7 +418,10 @@ int hrt_batch_run(hrt_batch* b, const int64_t* n_packets, int max_iter, const hr
     b->launch = launch_from(P, b->launch);
     if (!b->exec) {
         rc = capture(b, P);
-        if (rc != HRT_OK) return rc;
+        if (rc != HRT_OK) {
+            if (prev >= 0) cudaSetDevice(prev);
+            return rc;
+        }
     }
     int iters = 0;
     bool timed_out = false;

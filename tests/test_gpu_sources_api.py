@@ -206,3 +206,18 @@ def test_peeloff_checks():
     assert peel() == hrt.HRT_OK
     st = m.run_iteration(peel=1, update_temperature=0)
     assert st["n_peel_crossings"] > 0
+
+
+def test_run_parameter_checks():
+    wl = W.tiny_sphere(n_packets=2000)
+    m = hrt.Model(wl)
+    nan = float("nan")
+    for bad in (dict(kernel=5), dict(quantity=2), dict(block_size=128), dict(blocks_per_sm=-1),
+                dict(regroup_threshold=33), dict(regroup_threshold=-1), dict(watchdog_ms=-1.0),
+                dict(watchdog_ms=nan), dict(q_thres=nan), dict(delta_thres=nan)):
+        with pytest.raises(hrt.HrtError) as e:
+            m.run_iteration(**bad)
+        assert e.value.code == hrt.HRT_EINVAL, bad
+    st = m.run_iteration(block_size=256, blocks_per_sm=2, regroup_threshold=32, quantity=1)
+    assert st["iteration"] == 0                       # the rejected calls ran nothing
+    assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
