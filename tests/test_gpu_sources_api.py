@@ -218,6 +218,6 @@ def test_run_parameter_checks():
         with pytest.raises(hrt.HrtError) as e:
             m.run_iteration(**bad)
         assert e.value.code == hrt.HRT_EINVAL, bad
-    st = m.run_iteration(block_size=256, blocks_per_sm=2, regroup_threshold=32, quantity=1)
+    st = m.run_iteration(block_size=256, blocks_per_sm=3, regroup_threshold=32, quantity=1)
     assert st["iteration"] == 0                       # the rejected calls ran nothing
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
