@@ -221,3 +221,23 @@ def test_run_parameter_checks():
     st = m.run_iteration(block_size=256, blocks_per_sm=3, regroup_threshold=32, quantity=1)
     assert st["iteration"] == 0                       # the rejected calls ran nothing
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
+
+
+def test_resume_from_saved_temperatures_repeats_the_iteration():
+    """Checkpoint/resume: the temperatures after iteration i and the iteration counter (which keys
+    the random streams) are the whole state a Lucy iteration starts from."""
+    wl = W.tiny_sphere(n_packets=50_000)
+    a = hrt.Model(wl)
+    a.run_iteration()
+    T1 = a.temperature()
+    st_a = a.run_iteration()
+    b = hrt.Model(wl)
+    b.set_temperature(T1)
+    b.set_iteration(1)
+    st_b = b.run_iteration()
+    assert st_b["iteration"] == st_a["iteration"] == 1
+    for k in ("n_crossings", "n_interactions", "n_scatter", "n_absorb"):
+        assert st_b[k] == st_a[k], k
+    np.testing.assert_allclose(b.absorbed(), a.absorbed(), rtol=1e-10, atol=1e-300)
+    np.testing.assert_allclose(b.temperature(), a.temperature(), rtol=1e-10)
+    assert st_b["Q"] == pytest.approx(st_a["Q"], rel=1e-9)
