@@ -127,13 +127,9 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     if (slot < (unsigned long long)a.peel_cap) {
                         PeelEvent e;
                         e.px = porg.x; e.py = porg.y; e.pz = porg.z;
-                        e.ci = pk.r.ci;
-                        e.i = (int16_t)pk.r.i; e.j = (int16_t)pk.r.j; e.k = (int16_t)pk.r.k;
-                        e.flags = (int16_t)((relocate ? 1 : 0) | (kind == PEEL_HG ? 2 : 0));
+                        e.ci = relocate ? -1 : pk.r.ci;
                         e.ux = uin.x; e.uy = uin.y; e.uz = uin.z;
-                        e.chi = pk.dust.chi;
-                        e.sbin = pk.sbin;
-                        e.pad = 0;
+                        e.nu = kind == PEEL_HG ? -pk.nu : pk.nu;
                         a.peel_q[slot] = e;
                         start_walk();
                         return;

@@ -120,16 +120,14 @@ enum Counter {
 constexpr int N_ESC_MU = 10;
 
 // A peel-off event queued by the propagation kernel of an imaging pass (Sect. 2.6.2): the peel
-// rays from it to every observer are walked by a separate pass, one ray per thread.
-struct PeelEvent {
+// rays from it to every observer are walked by a separate pass, one ray per thread.  The record
+// is 32 bytes, one memory sector: the per-axis cell indices follow from the linear index, and the
+// extinction and SED bin from the frequency, through the same functions the packet used.
+struct __align__(16) PeelEvent {
     float px, py, pz;              // event position (scaled)
-    int32_t ci;                    // its cell (linear; unused when relocating)
-    int16_t i, j, k;               // its cell per axis
-    int16_t flags;                 // bit 0: locate the cell along the observer direction; bit 1: HG
+    int32_t ci;                    // its cell (linear), or -1: locate the cell along each observer direction
     float ux, uy, uz;              // incoming direction (Henyey-Greenstein scattering)
-    float chi;                     // extinction at the packet frequency
-    int32_t sbin;                  // SED bin of the packet frequency
-    int32_t pad;
+    float nu;                      // packet frequency; negated for a scattering (Henyey-Greenstein weight)
 };
 
 struct RunArgs {

@@ -25,7 +25,7 @@ __device__ __forceinline__ unsigned long long queued_events(const RunArgs& a) {
 
 // bucket of an event: its cell, or ncells for an event located along each observer direction
 __device__ __forceinline__ int64_t peel_key(const PeelEvent& e, int64_t ncells) {
-    return (e.flags & 1) ? ncells : (int64_t)e.ci;
+    return e.ci < 0 ? ncells : (int64_t)e.ci;
 }
 
 __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_sums) {
@@ -117,20 +117,27 @@ __global__ void __launch_bounds__(256, PEEL_MINB)
         const int ob = (int)(q / n_ev);
         const PeelEvent e = a.peel_q[order[q - (unsigned long long)ob * n_ev]];
         const float3 n = make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2));
+        // the packet's extinction and SED bin, recomputed from its frequency by the same functions
+        const float nu = fabsf(e.nu);
+        const int sbin = sed_bin(o, nu);
+        if (sbin < 0) continue;                             // (never queued)
+        const float chi = dust_at(d, nu).chi;
         Ray r;
         r.p = make_float3(e.px, e.py, e.pz);
-        r.i = e.i;
-        r.j = e.j;
-        r.k = e.k;
         r.ci = e.ci;
+        if (e.ci >= 0) {
+            r.i = e.ci % g.n1;
+            r.j = (e.ci / g.n1) % g.n2;
+            r.k = e.ci / (g.n1 * g.n2);
+        }
         set_dir(r, n);
         float tau = 0.f;
-        if (!(e.flags & 1) || grid_locate<G>(g, r)) {
+        if (e.ci >= 0 || grid_locate<G>(g, r)) {
             int zero_run = 0;
             for (unsigned steps = 0;;) {
                 int axis, dir;
                 const float l = cell_exit<G>(g, r, axis, dir);
-                tau += __ldg(g.rhoL + r.ci) * e.chi * l;
+                tau += __ldg(g.rhoL + r.ci) * chi * l;
                 lc.v[C_PEEL_CROSSINGS]++;
                 if (tau > PEEL_TAU_STOP) break;             // < 4e-18 of the weight remains
                 if (cell_step<G>(g, r, l, axis, dir)) break;
@@ -145,10 +152,10 @@ __global__ void __launch_bounds__(256, PEEL_MINB)
                 }
             }
         }
-        const float prob = (e.flags & 2) ? hg_phase(d.g, dot3(make_float3(e.ux, e.uy, e.uz), n)) : (0.25f / CUDART_PI_F);
+        const float prob = (e.nu < 0.f) ? hg_phase(d.g, dot3(make_float3(e.ux, e.uy, e.uz), n)) : (0.25f / CUDART_PI_F);
         const double w = a.eps * (double)(prob * expf(-tau));
-        if (st.sed) atomicAdd(st.sed + ob * o.nsed + e.sbin, w);
-        else atomicAdd(t.sed + (int64_t)ob * o.nsed + e.sbin, w);
+        if (st.sed) atomicAdd(st.sed + ob * o.nsed + sbin, w);
+        else atomicAdd(t.sed + (int64_t)ob * o.nsed + sbin, w);
         if (o.nimg > 0) {
             const float px = e.px * __ldg(o.ex + 3 * ob) + e.py * __ldg(o.ex + 3 * ob + 1) + e.pz * __ldg(o.ex + 3 * ob + 2);
             const float py = e.px * __ldg(o.ey + 3 * ob) + e.py * __ldg(o.ey + 3 * ob + 1) + e.pz * __ldg(o.ey + 3 * ob + 2);
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(256, PEEL_MINB)
             const int iy = (int)floorf((py + o.img_half) * o.img_scale);
             if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
                 for (int l = 0; l < o.nimg; ++l)
-                    if (__ldg(o.img_bin + l) == e.sbin)
+                    if (__ldg(o.img_bin + l) == sbin)
                         atomicAdd(t.img + (((int64_t)ob * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
         }
     }
