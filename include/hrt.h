@@ -255,6 +255,19 @@ int hrt_set_temperature(hrt_ctx* ctx, const double* T, int64_t n);
 int hrt_set_temperature_device(hrt_ctx* ctx, const double* d_T, int64_t n);
 /* Set the iteration counter (it keys the random streams, so a resumed run repeats them). */
 int hrt_set_iteration(hrt_ctx* ctx, int iteration);
+/* Resume: the rest of the state the next iteration starts from.  A Lucy iteration i reads the
+ * temperatures after iteration i-1 (hrt_set_temperature), the iteration counter
+ * (hrt_set_iteration), the specific energies Adot after iteration i-1 (Eq. 2, erg s^-1 g^-1,
+ * [ncells] C order, finite >= 0; read by the convergence statistic when it is taken on Adot,
+ * quantity 1) and the previous percentile Q^{i-1} with whether it exists (Eqs. 5-6: Delta =
+ * max(Q^{i-1}/Q^i, Q^i/Q^{i-1})).  Save them with hrt_get_temperature, hrt_get_specific_energy and
+ * hrt_get_convergence_state after iteration i-1 and set all four to repeat iteration i exactly
+ * (Q, Delta and the converged flag included).  Inputs are copied.  Q_prev >= 1 or +inf when
+ * have_Q != 0 (else HRT_EINVAL); have_Q = 0 forgets Q^{i-1} (Delta is then +inf).  Setting the
+ * grid clears the convergence state; a new grid starts with Adot = 0. */
+int hrt_set_specific_energy(hrt_ctx* ctx, const double* adot, int64_t n);
+int hrt_set_convergence_state(hrt_ctx* ctx, int have_Q, double Q_prev);
+int hrt_get_convergence_state(hrt_ctx* ctx, int* have_Q, double* Q_prev);
 int hrt_set_model_id(hrt_ctx* ctx, uint32_t model_id);
 
 /* ------------------------------------------------------------------ single steps (test hooks)
@@ -348,7 +361,11 @@ int hrt_net_warm_start(hrt_net* net, hrt_ctx* ctx);
  * bias and optional ReLU (Cin % 16 == 0, Cout % 32 == 0), and its input, weight and bias
  * gradients for an output gradient dy (Cin, Cout % 32 == 0).  Weights [27][Cin][Cout].  The
  * convolutions run on the tcgen05 tensor cores (accumulator in tensor memory); HRT_ETIMEDOUT if
- * one of their bounded waits gave up.  hrt_nn_conv3d_mma is the same forward convolution with
+ * one of their bounded waits gave up.  That is a last resort (a wait of seconds that a healthy
+ * GPU never reaches): the block that gave up frees its tensor memory while its own MMAs may
+ * still be running, so treat the outputs of that call, and of any later tensor-core call in the
+ * process, as invalid; the network calls (hrt_net_*) return the same code and leave the weights
+ * of a failed training step unchanged, and the caller should recompute or stop.  hrt_nn_conv3d_mma is the same forward convolution with
  * warp-level mma.sync, the baseline the tcgen05 kernel is measured against. */
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
                   int relu, float* d_y, void* stream);
@@ -375,8 +392,12 @@ int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const 
  * threads) race and give wrong results; serialise them.
  *
  * Limit: 1 <= n <= HRT_NOALLOC_MAX_CELLS (2^31 - 1, the range of its 32-bit bin counts).
- * Returns HRT_OK, HRT_EINVAL (n out of range, a null pointer, p outside (0, 1]) or HRT_ECUDA;
- * it has no context, so hrt_last_error() does not describe its failures. */
+ * Returns HRT_OK; HRT_EINVAL (n out of range, a null pointer, p outside (0, 1]); HRT_ESTATE when
+ * a CUDA error from earlier work on the calling thread is already pending (nothing is launched
+ * and that error is left in place for the caller to read with cudaGetLastError); or HRT_ECUDA
+ * when the device query or one of its own launches fails (that launch error is cleared).  A
+ * sticky error (a fault in any earlier kernel of the process) makes it return HRT_ESTATE or
+ * HRT_ECUDA as well.  It has no context, so hrt_last_error() does not describe its failures. */
 #define HRT_NOALLOC_MAX_CELLS 2147483647LL
 int hrt_quantile_ratio_noalloc(int64_t n, const double* d_prev, const double* d_cur, const float* d_rho,
                                double p, double* d_out, void* stream);

@@ -856,9 +856,9 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         job.src.col = ctx->d_src_col.p;
         launched++;
     }
-    if (A.peel && P.kernel != HRT_KERNEL_PLAIN && ctx->grid.n1 < 32768 && ctx->grid.n2 < 32768 && ctx->grid.n3 < 32768) {
-        // queue for the peel pass (16-bit cell indices per axis): two events per packet (an
-        // overflow is peeled inline), at most 2^27 events (6 GiB)
+    if (A.peel && P.kernel != HRT_KERNEL_PLAIN) {
+        // queue for the peel pass: two events per packet (an overflow is peeled inline), at most
+        // 2^27 events (4 GiB of 32-byte records)
         const int64_t cap = P.peel_queue_events > 0
                                 ? std::min<int64_t>(P.peel_queue_events, (int64_t)1 << 27)
                                 : std::min<int64_t>(std::max<int64_t>(2 * n_packets, (int64_t)1 << 20), (int64_t)1 << 27);
@@ -1194,6 +1194,38 @@ int hrt_get_watchdog_report(hrt_ctx* ctx, float* out, int64_t n) {
 int hrt_set_iteration(hrt_ctx* ctx, int iteration) {
     if (!ctx || iteration < 0) return HRT_EINVAL;
     ctx->iteration = iteration;
+    return HRT_OK;
+}
+
+int hrt_set_specific_energy(hrt_ctx* ctx, const double* adot, int64_t n) {
+    if (!ctx) return HRT_EINVAL;
+    if (ctx->gtype < 0 || (int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "set grid and density first");
+    if (!adot || n != ctx->ncells())
+        return ctx->fail(HRT_EINVAL, "specific energy: expected %lld cells", (long long)ctx->ncells());
+    for (int64_t c = 0; c < n; ++c)
+        if (!(adot[c] >= 0) || !std::isfinite(adot[c])) return ctx->fail(HRT_EINVAL, "specific energy must be finite >= 0");
+    DeviceGuard dg(ctx->device);
+    if (ctx->dirty_grid) {
+        int rc = stage_grid(ctx);
+        if (rc != HRT_OK) return rc;
+    }
+    CK(ctx->d_adot.upload(adot, n, ctx->stream), "upload adot");
+    CK(cudaStreamSynchronize(ctx->stream), "upload adot");
+    return HRT_OK;
+}
+
+int hrt_set_convergence_state(hrt_ctx* ctx, int have_Q, double Q_prev) {
+    if (!ctx) return HRT_EINVAL;
+    if (have_Q && !(Q_prev >= 1.0)) return ctx->fail(HRT_EINVAL, "Q_prev must be >= 1 (a ratio max(a/b, b/a)) or +inf");
+    ctx->have_Q = have_Q != 0;
+    ctx->Q_prev = have_Q ? Q_prev : std::numeric_limits<double>::infinity();
+    return HRT_OK;
+}
+
+int hrt_get_convergence_state(hrt_ctx* ctx, int* have_Q, double* Q_prev) {
+    if (!ctx || !have_Q || !Q_prev) return HRT_EINVAL;
+    *have_Q = ctx->have_Q ? 1 : 0;
+    *Q_prev = ctx->Q_prev;
     return HRT_OK;
 }
 

@@ -98,6 +98,9 @@ _SIGS = {
     "hrt_set_temperature_device": (C.c_int, [_vp, _vp, _i64]),
     "hrt_get_watchdog_report": (C.c_int, [_vp, _vp, _i64]),
     "hrt_set_iteration": (C.c_int, [_vp, C.c_int]),
+    "hrt_set_specific_energy": (C.c_int, [_vp, _vp, _i64]),
+    "hrt_set_convergence_state": (C.c_int, [_vp, C.c_int, C.c_double]),
+    "hrt_get_convergence_state": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hrt_set_model_id": (C.c_int, [_vp, C.c_uint32]),
     "hrt_step_philox": (C.c_int, [_i64, _vp, _vp, _vp, _vp]),
     "hrt_step_cell_exit": (C.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
@@ -296,6 +299,18 @@ class Model:
 
     def set_iteration(self, i):
         check(self.ctx, load().hrt_set_iteration(self.ctx, int(i)))
+
+    def set_specific_energy(self, adot):
+        adot = _c64(adot).reshape(-1)
+        check(self.ctx, load().hrt_set_specific_energy(self.ctx, _ptr(adot), adot.size))
+
+    def convergence_state(self):
+        have, q = C.c_int(), C.c_double()
+        check(self.ctx, load().hrt_get_convergence_state(self.ctx, C.byref(have), C.byref(q)))
+        return int(have.value), float(q.value)
+
+    def set_convergence_state(self, have_Q, Q_prev):
+        check(self.ctx, load().hrt_set_convergence_state(self.ctx, int(have_Q), float(Q_prev)))
 
     def tables(self):
         nT, nnu = len(self.wl.T_nodes), len(self.wl.nu)

@@ -2,6 +2,8 @@
 of their own (against the oracle's table of it, step by step and over a whole iteration), the
 model id that keys the random streams, clearing and re-adding sources, the library stream, the
 device read-out of the SEDs and the watchdog report."""
+import math
+
 import numpy as np
 import pytest
 
@@ -223,21 +225,60 @@ def test_run_parameter_checks():
     assert st["e_escaped"] + st["e_killed"] == pytest.approx(st["e_emitted"], rel=1e-12)
 
 
-def test_resume_from_saved_temperatures_repeats_the_iteration():
-    """Checkpoint/resume: the temperatures after iteration i and the iteration counter (which keys
-    the random streams) are the whole state a Lucy iteration starts from."""
+@pytest.mark.parametrize("quantity", [0, 1])
+def test_resume_from_saved_temperatures_repeats_the_iteration(quantity):
+    """Checkpoint/resume: the temperatures and specific energies after iteration i-1, the
+    iteration counter (which keys the random streams) and the previous percentile Q^{i-1} (Eqs.
+    5-6) are the whole state Lucy iteration i starts from; with them a fresh context repeats the
+    iteration, its Q, Delta and converged flag included, for T and for Adot as the quantity."""
     wl = W.tiny_sphere(n_packets=50_000)
+    kw = dict(quantity=quantity, q_thres=10.0, delta_thres=10.0)
     a = hrt.Model(wl)
-    a.run_iteration()
-    T1 = a.temperature()
-    st_a = a.run_iteration()
+    a.run_iteration(**kw)
+    a.run_iteration(**kw)
+    T2, A2, conv = a.temperature(), a.specific_energy(), a.convergence_state()
+    assert conv[0] == 1 and 1.0 <= conv[1] < math.inf
+    st_a = a.run_iteration(**kw)
     b = hrt.Model(wl)
-    b.set_temperature(T1)
-    b.set_iteration(1)
-    st_b = b.run_iteration()
-    assert st_b["iteration"] == st_a["iteration"] == 1
+    b.set_temperature(T2)
+    b.set_specific_energy(A2)
+    b.set_iteration(2)
+    b.set_convergence_state(*conv)
+    st_b = b.run_iteration(**kw)
+    assert st_b["iteration"] == st_a["iteration"] == 2
     for k in ("n_crossings", "n_interactions", "n_scatter", "n_absorb"):
         assert st_b[k] == st_a[k], k
     np.testing.assert_allclose(b.absorbed(), a.absorbed(), rtol=1e-10, atol=1e-300)
     np.testing.assert_allclose(b.temperature(), a.temperature(), rtol=1e-10)
+    np.testing.assert_allclose(b.specific_energy(), a.specific_energy(), rtol=1e-10, atol=1e-300)
+    assert math.isfinite(st_a["Q"]) and math.isfinite(st_a["Delta"])
     assert st_b["Q"] == pytest.approx(st_a["Q"], rel=1e-9)
+    assert st_b["Delta"] == pytest.approx(st_a["Delta"], rel=1e-9)
+    assert st_b["converged"] == st_a["converged"] == 1
+    # without the saved percentile, Delta is unknown and the run is not converged
+    c = hrt.Model(wl)
+    c.set_temperature(T2)
+    c.set_specific_energy(A2)
+    c.set_iteration(2)
+    st_c = c.run_iteration(**kw)
+    assert st_c["Q"] == pytest.approx(st_a["Q"], rel=1e-9)
+    assert math.isinf(st_c["Delta"]) and st_c["converged"] == 0
+
+
+def test_resume_setters_check_their_arguments():
+    wl = W.tiny_sphere(n_packets=1000)
+    m = hrt.Model(wl)
+    for have, q in ((1, 0.5), (1, float("nan"))):
+        with pytest.raises(hrt.HrtError) as e:
+            m.set_convergence_state(have, q)
+        assert e.value.code == hrt.HRT_EINVAL
+    m.set_convergence_state(1, math.inf)
+    assert m.convergence_state() == (1, math.inf)
+    m.set_convergence_state(0, 0.0)
+    assert m.convergence_state() == (0, math.inf)
+    bad = np.full(m.ncells, 1.0)
+    bad[3] = -1.0
+    for arr in (bad, np.full(m.ncells - 1, 1.0)):
+        with pytest.raises(hrt.HrtError) as e:
+            m.set_specific_energy(arr)
+        assert e.value.code == hrt.HRT_EINVAL
