@@ -420,8 +420,9 @@ int hrt_net_forward(hrt_net* n, int N, int D, int H, int W, const float* d_in, f
     rc = forward(n);
     if (rc != HRT_OK) return rc;
     NCK(cudaMemcpyAsync(d_out, n->y, NV * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
-    NCK(cudaStreamSynchronize(n->stream));
-    return HRT_OK;
+    int failed = 0;
+    NCK(nn::tc_status(&failed, n->stream));     // synchronises the stream
+    return failed ? HRT_ETIMEDOUT : HRT_OK;
 }
 
 static int grad_pass(hrt_net* n, int N, int D, int H, int W, const float* d_in, const float* d_target, double* loss_out) {
@@ -438,6 +439,10 @@ static int grad_pass(hrt_net* n, int N, int D, int H, int W, const float* d_in, 
     NCK(nn::mse_loss(n->y, n->tf, n->dy, n->loss, NV, n->stream));
     rc = backward(n);
     if (rc != HRT_OK) return rc;
+    // a tensor-core wait that gave up leaves the gradients invalid: no step is taken on them
+    int failed = 0;
+    NCK(nn::tc_status(&failed, n->stream));
+    if (failed) return HRT_ETIMEDOUT;
     if (loss_out) {
         NCK(cudaMemcpyAsync(loss_out, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
         NCK(cudaStreamSynchronize(n->stream));
@@ -525,6 +530,9 @@ int hrt_net_warm_start(hrt_net* n, hrt_ctx* ctx) {
     rc = forward(n);
     n->stream = keep;
     if (rc != HRT_OK) return rc;
+    int failed = 0;
+    CK(nn::tc_status(&failed, ctx->stream), "warm start");
+    if (failed) return ctx->fail(HRT_ETIMEDOUT, "a tensor-core wait gave up; the temperatures are unchanged");
     k_to_temperature<<<512, 256, 0, ctx->stream>>>(n->y, ctx->d_T.p, ctx->ncells(), ctx->Tn.front(), ctx->Tn.back());
     CK(cudaStreamSynchronize(ctx->stream), "warm start");
     ctx->have_T = true;

@@ -121,13 +121,18 @@ extern "C" int hrt_quantile_ratio_noalloc(int64_t n, const double* d_prev, const
     if (n < 1 || n > HRT_NOALLOC_MAX_CELLS) return HRT_EINVAL;
     if (!d_prev || !d_cur || !d_rho || !d_out) return HRT_EINVAL;
     if (!(p > 0.0 && p <= 1.0)) return HRT_EINVAL;
+    // an error left by earlier work on this thread is the caller's: report it apart and leave it
+    if (cudaPeekAtLastError() != cudaSuccess) return HRT_ESTATE;
     int err = HRT_OK;
     NoAllocScratch* s = scratch_for_current_device(&err);
     if (!s) return err;
     const cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return HRT_ECUDA;
+    }
     const long long need = (n + 255) / 256;
     const int grid = (int)(need < (long long)sms * 8 ? need : (long long)sms * 8);
     na_init<<<1, 256, 0, st>>>(s);
