@@ -103,18 +103,39 @@ def _brute_sph(walls, p, u):
     t_exit = -b + math.sqrt(b * b - (pp - rw[-1] ** 2))
     ts = sorted(set(t for t in ts if t <= t_exit) | {t_exit})
     n = [len(rw) - 1, len(tw) - 1, len(pw) - 1]
-    segs = []
-    for t0, t1 in zip(ts[:-1], ts[1:]):
-        q = p + 0.5 * (t0 + t1) * u
+
+    def cell(q):
         r = math.sqrt(float(q @ q))
         if r < rw[0]:
-            continue                      # the inner hole holds no cell
+            return None                   # the inner hole holds no cell
         th = math.acos(max(-1.0, min(1.0, q[2] / r)))
         ph = math.atan2(q[1], q[0]) % (2 * math.pi)
         i = int(np.searchsorted(rw, r, side="right") - 1)
         j = int(np.searchsorted(tw, th, side="right") - 1)
         k = int(np.searchsorted(pw, ph, side="right") - 1) if n[2] > 1 else 0
-        segs.append(((k * n[1] + j) * n[0] + i, t1 - t0))
+        return (k * n[1] + j) * n[0] + i
+
+    # The crossings above are pinned without their coefficients: every crossing lies on one of
+    # the wall surfaces (its polar angle, radius or azimuth equals a wall's), and no wall is
+    # crossed inside a sub-segment (points spread along it all fall in its midpoint's cell), so
+    # a wrong coefficient or nappe choice, or a missed root, fails here and not only in the oracle.
+    for t in ts[1:-1]:
+        q = p + t * u
+        r = math.sqrt(float(q @ q))
+        th = math.acos(max(-1.0, min(1.0, q[2] / r)))
+        ph = math.atan2(q[1], q[0]) % (2 * math.pi)
+        on = (np.min(np.abs(rw - r)) <= 1e-12 * rw[-1]
+              or np.min(np.abs(tw[1:-1] - th)) <= 1e-9
+              or (len(pw) > 2 and np.min(np.abs(np.angle(np.exp(1j * (pw - ph))))) <= 1e-9))
+        assert on, ("crossing on no wall", p, u, t)
+    segs = []
+    for t0, t1 in zip(ts[:-1], ts[1:]):
+        c = cell(p + 0.5 * (t0 + t1) * u)
+        for f in (0.02, 0.1, 0.25, 0.4, 0.6, 0.75, 0.9, 0.98):
+            if t1 - t0 > 1e-9 * rw[-1]:
+                assert cell(p + (t0 + f * (t1 - t0)) * u) == c, ("wall inside a segment", p, u, t0, t1, f)
+        if c is not None:
+            segs.append((c, t1 - t0))
     return segs
 
 
