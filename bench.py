@@ -1,26 +1,37 @@
 #!/usr/bin/env python
 """Benchmark: photon packets/s and time-to-converged temperature on one GB300.
 
-Workload (one "step"): the flared passive disk on a spherical-polar grid (nr = 200 log-spaced
-over 1-1000 AU, ntheta = 128 concentrated at the midplane, nphi = 1, rho ~ r^-1 exp(-z^2/2h^2),
-h = 10 AU (r/100 AU)^1.125, radial 550 nm optical depth 100), a 5800 K 1 Lsun star, 1e7 packets
-per Lucy iteration, 10 iterations, then one peel-off pass of 1e7 packets into SEDs at 10
-inclinations x 250 wavelength bins.  Inputs are synthetic (no dataset).
+Workload (one "step", the default ``--workload cloud``): the 3D turbulent cloud, a Cartesian
+256^3 grid over a 0.65 pc box with rho = exp(1.5 G), G a k^-11/3 Gaussian random field scaled to
+a mean 550 nm optical depth of 10 across the box, 20 stars uniform in the box (T 3000-20000 K,
+L 0.1-100 Lsun).  A step is the solve: ``--iters`` (5) Lucy iterations of 1e8 packets from the
+10 K cold start, then one imaging pass of 1e8 packets peeled off into 512 x 512 images at 6
+wavelengths (1.25, 3.6, 8, 70, 250, 500 um) and the SED at (theta, phi) = (45, 45) degrees.
+The cloud's density (64 MiB) and FP64 accumulators (128 MiB) exceed L2.  Inputs are synthetic.
 
-value     packets propagated per second over the whole step (iterations + peel-off pass), device
-          time by CUDA events on the library's stream, inputs resident in HBM; L2 is flushed
-          between timed steps (the disk's cell data fit in L2).
+value     packets propagated per second over the whole step (Lucy iterations + imaging pass),
+          device time by CUDA events on the library's stream, inputs resident in HBM; L2 is
+          flushed (256 MiB write) between timed steps.
 e2e       the same step through the C ABI with host buffers: density and starting temperatures
-          copied from pinned host memory, temperatures and SEDs copied back, all inside the
-          timed region.
-roofline  the propagation kernel: algorithmic bytes per launch (20 B per packet cell crossing:
-          FP32 density + FP64 accumulator read-modify-write; 4 B per peel-off crossing; 400 B per
-          re-emission row) over its measured duration, against the measured HBM copy bandwidth.
-time_to_converged_ms      device time of the Lucy iterations until the 99th percentile of the
-          iteration change in T is below 2 % (null when the 10 iterations never get there: the
-          Monte-Carlo noise of the disk's optically thick midplane is then the floor).
-time_to_converged_pda_ms  the same from a separate solve (not in `value`) in which cells entered
-          by fewer than --pda-min packets take the partial diffusion approximation (App. A).
+          copied from pinned host memory, temperatures, SED and images copied back, all inside
+          the timed region.
+roofline  the Lucy propagation kernel (k_event, one launch per iteration): algorithmic bytes per
+          launch (20 B per cell crossing: FP32 density + FP64 accumulator read-modify-write;
+          400 B per re-emission row) over its CUDA-event duration, against the measured HBM copy
+          bandwidth.  `traffic` is the DRAM bytes ncu measured per launch (summary under profiles/).
+time_to_converged_ms        device time of the Lucy iterations until the 99th percentile of the
+          iteration change of T is below 2 % (Q_99(dT) < 1.02, Eqs. 4-5); null when the Monte-Carlo
+          noise floor of Q_99 lies above 1.02 at this packet count (`q99_history` shows the floor).
+time_to_converged_delta_ms  the same until the 99th percentile itself changes by less than 2 %
+          between iterations (Eq. 6's Delta test, with Q_99 < 2): the iteration has reached its
+          noise floor.
+plain_gpu  the same step with the one-thread-per-history kernel (k_plain).
+cpu_baseline  the FP64 oracle on all host cores on the same mix of passes: a packet sample of a
+          cold-start Lucy iteration, of a Lucy iteration at the oracle's own later temperatures and
+          of the imaging pass, each rate weighted by the step's packets in that kind of pass.
+flared_disk  the L2-resident workload (spherical 200 x 128 x 1 disk, 1e7 packets x 10 iterations
+          + a peel-off pass at 10 inclinations x 250 bins), with its kernel's L2 bytes and FP64
+          atomics against an L2 copy and an L2 FP64 atomic rate measured in the same process.
 
 ``--rows`` instead measures the extensions of the method on their own workloads (one JSON line, not
 the headline): the modified random walk against the plain walk on thick grey models and an
@@ -29,13 +40,12 @@ cylindrical disk and the clouds in an external radiation field.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference implementation of this build) on
 the host cores on a bounded sample of the same workload.  N > 1 GPUs (torchrun) run independent
-disk models, one per rank (weak scaling, no collective).
+models, one per rank (weak scaling, no collective).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -46,18 +56,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "photon packets/sec (flared-disk Lucy solve + peel-off SEDs)"
+METRIC = "photon packets/sec (Lucy solve + peel-off imaging pass)"
 UNIT = "packets/s"
 B_CROSS = 20.0
 B_PEEL = 4.0
 B_REEMIT = 400.0
-# DRAM bytes (read + write) per propagation launch, averaged over a step's 12 launches (10 Lucy
-# iterations, the imaging pass and its peel pass), from an ncu capture of the current kernels on
-# a 2e5-packet case of this workload scaled to 1e7 packets: the Lucy launches touch the resident
-# grid and tables once (0.58 MB, independent of the packet count); the peel-event queue (48 B
-# per event, 4.74e6 events) and its cell order grow with the packets: 228 MB written by the
-# imaging pass, 247 MB read by the peel pass
-TRAFFIC_PER_LAUNCH = 40.1e6
+# DRAM bytes (read + write) per crossing of the Lucy propagation kernel on the 256^3 cloud, from
+# an ncu capture of the current k_event (a 1e6-packet Lucy launch on the full grid; DRAM traffic
+# there comes from the cache misses of the walk, so it grows with the crossings): per launch =
+# this x the launch's crossings
+TRAFFIC_PER_CROSSING = None
 
 
 def parse():
@@ -66,32 +74,52 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cloud", "disk"], default="cloud")
     ap.add_argument("--kernel", choices=["event", "plain"], default="event")
-    ap.add_argument("--packets", type=int, default=10_000_000)
-    ap.add_argument("--iters", type=int, default=10)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
+    ap.add_argument("--packets", type=int, default=None, help="packets per pass (cloud 1e8, disk 1e7)")
+    ap.add_argument("--iters", type=int, default=None, help="Lucy iterations per step (cloud 5, disk 10)")
+    ap.add_argument("--cpu-seconds", type=float, default=18.0, help="target length of the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain-kernel arm and the disk line")
     ap.add_argument("--rows", action="store_true",
                     help="measure the extension rows (MRW, raytracing, cylindrical grids, external field) instead")
     ap.add_argument("--pda-min", type=int, default=6000,
-                    help="packet entries below which a cell takes the diffusion approximation in the "
-                         "time-to-converged solve with PDA (App. A); 0 skips that solve")
-    return ap.parse_args()
+                    help="disk line: packet entries below which a cell takes the diffusion approximation in "
+                         "the time-to-converged solve with PDA (App. A); 0 skips that solve")
+    a = ap.parse_args()
+    if a.packets is None:
+        a.packets = 100_000_000 if a.workload == "cloud" else 10_000_000
+    if a.iters is None:
+        a.iters = 5 if a.workload == "cloud" else 10
+    return a
 
 
-def workload(n_packets, rank=0):
+def workload(n_packets, rank=0, name="cloud"):
+    """The step's model; rank r of a multi-GPU run gets its own seed (an independent model)."""
     from paper_1112_1071_gb300 import workloads as W
+    if name == "cloud":
+        return W.turbulent_cloud(n_packets=n_packets, seed=4 + rank)
     return W.flared_disk(n_packets=n_packets, seed=2 + rank)
 
 
+def describe(name, packets, iters):
+    if name == "cloud":
+        return (f"turbulent_cloud Cartesian 256^3, 0.65 pc, sigma_lnrho=1.5, mean tau_550=10, 20 stars; "
+                f"{packets:.0e} packets x {iters} Lucy iterations from 10 K + 1 imaging pass "
+                f"(512x512 images at 6 wavelengths, 1 observer)")
+    return (f"flared_disk spherical 200x128x1, tau_550=100, 1 star; {packets:.0e} packets x {iters} Lucy "
+            f"iterations from 10 K + 1 peel-off pass (10 inclinations x 250 bins)")
+
+
 def config(args, world):
-    return {"workload": "flared_disk spherical 200x128x1, tau_550=100, 1 star; "
-                        f"{args.packets:.0e} packets x {args.iters} Lucy iterations + 1 peel-off pass "
-                        "(10 inclinations x 250 bins)",
-            "grid": "spherical-polar nr=200 ntheta=128 nphi=1", "packets_per_iteration": args.packets,
-            "iterations": args.iters, "observers": 10, "sed_bins": 250,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
-            "kernel": args.kernel}
+    c = {"workload": describe(args.workload, args.packets, args.iters), "packets_per_iteration": args.packets,
+         "iterations": args.iters, "l2": "flushed between timed steps (256 MiB write)",
+         "parallelism": f"replicas x{world}", "kernel": args.kernel}
+    if args.workload == "cloud":
+        c.update(grid="cartesian 256x256x256", sources=20, images="6 x 512 x 512", observers=1, sed_bins=250)
+    else:
+        c.update(grid="spherical-polar nr=200 ntheta=128 nphi=1", observers=10, sed_bins=250)
+    return c
 
 
 def job_throughput(total_ms, e2e_ms, world, packets_step, steps, dist=None, device="cpu"):
@@ -105,6 +133,23 @@ def job_throughput(total_ms, e2e_ms, world, packets_step, steps, dist=None, devi
         total_ms, e2e_ms = float(tt[0]), float(tt[1])
     value = world * packets_step * steps / (total_ms * 1e-3)
     return value, world * packets_step / (e2e_ms * 1e-3), total_ms, e2e_ms
+
+
+def converged_at(qs, ms, q_thres=1.02, delta_thres=None):
+    """First iteration (1-based, at least the 2nd) that meets the criterion, and the device time
+    of the iterations up to it: Q_99 < q_thres, and with delta_thres also Delta = max(Q_prev/Q,
+    Q/Q_prev) < delta_thres (Eqs. 5-6).  (None, None) when no iteration meets it."""
+    t = 0.0
+    for i, (q, m) in enumerate(zip(qs, ms)):
+        t += m
+        if i == 0:
+            continue
+        ok = q < q_thres
+        if delta_thres is not None:
+            ok = ok and max(qs[i - 1] / q, q / qs[i - 1]) < delta_thres
+        if ok:
+            return i + 1, t
+    return None, None
 
 
 # ------------------------------------------------------------------ clocks
@@ -158,48 +203,291 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def cpu_oracle_rate(args, seconds):
+_ORACLE_CACHE = {}
+
+
+def cpu_oracle_rate(wl, iters, seconds, cores=None, refresh=False):
     """Packets/s of the FP64 oracle on all host cores (threads over packet ranges with private
-    accumulators), one Lucy iteration of the disk at its cold-start temperatures, on a packet
-    sample sized to take about `seconds`."""
+    accumulators) on the step's mix of passes: the cold-start Lucy iteration, a Lucy iteration at
+    the oracle's own temperatures after it (the later iterations) and the imaging pass at those
+    temperatures.  The first call times each kind of pass at two packet counts, which separates
+    its fixed cost (per-thread accumulators over every cell, their sum, the temperature update)
+    from its cost per packet; refresh=True re-times one sample of each kind and updates the cost
+    per packet (the fixed costs are kept).  The step's CPU time is the sum over its passes of
+    (fixed + packets x per packet), for 1, iters - 1 and 1 passes of wl.n_packets; the samples
+    take about seconds / 3 each.  Returns (rate, cores, description)."""
     from oracle.mc import OracleModel
-    wl = workload(args.packets)
-    om = OracleModel(wl)
-    cores = os.cpu_count() or 1
-    n = 20_000
-    t0 = time.perf_counter()
-    om.run_packets(n, 0, nthreads=cores)
-    dt = time.perf_counter() - t0
-    n2 = int(min(max(n, n * seconds / max(dt, 1e-3)), args.packets))
-    t0 = time.perf_counter()
-    om.run_packets(n2, 0, nthreads=cores)
-    dt2 = time.perf_counter() - t0
-    return n2 / dt2, cores, n2, dt2
+    cores = cores or os.cpu_count() or 1
+    st = _ORACLE_CACHE.get(id(wl))
+    if st is None:
+        st = _ORACLE_CACHE[id(wl)] = {"om": OracleModel(wl)}
+    om = st["om"]
+    part = max(seconds / 3.0, 0.05)
+
+    def cold(n):
+        om.T[:] = 10.0
+        om.iteration, om.Q_prev = 0, None
+        om.run_iteration(n_packets=n, nthreads=cores)
+
+    def lucy(n):
+        om.T[:] = st["T1"]
+        om.run_packets(n, st["it1"], nthreads=cores)
+
+    def imaging(n):
+        om.T[:] = st["T1"]
+        om.run_packets(n, 0x80000000 | st["it1"], peel=True, nthreads=cores)
+
+    def timed(fn, n):
+        t0 = time.perf_counter()
+        fn(n)
+        return time.perf_counter() - t0
+
+    def model(fn):
+        n0 = max(256, cores * 16)
+        t0 = timed(fn, n0)
+        n1 = 8 * n0
+        per = max((timed(fn, n1) - t0) / (n1 - n0), 1e-9)
+        n2 = int(min(max(n1, n0 + part / per), wl.n_packets))
+        t2 = timed(fn, n2)
+        per = max((t2 - t0) / (n2 - n0), 1e-9)
+        return [max(t0 - per * n0, 0.0), per, n2, t2]
+
+    kinds = (("cold", cold), ("lucy", lucy), ("imaging", imaging))
+    if "cost" not in st:
+        st["cost"] = {}
+        st["cost"]["cold"] = model(cold)
+        cold(max(256, min(wl.n_packets, int(part / st["cost"]["cold"][1]))))    # the later passes' T
+        st["T1"], st["it1"] = om.T.copy(), om.iteration
+        st["cost"]["lucy"] = model(lucy)
+        st["cost"]["imaging"] = model(imaging)
+    elif refresh:
+        for name, fn in kinds:
+            c = st["cost"][name]
+            n = int(min(max(256, part / c[1]), wl.n_packets))
+            t = timed(fn, n)
+            c[1], c[2], c[3] = max((t - c[0]) / n, 1e-9), n, t
+    (f1, c1, n1, t1), (f2, c2, n2, t2), (f3, c3, n3, t3) = (st["cost"][k] for k, _ in kinds)
+    N = wl.n_packets
+    t_step = (f1 + N * c1) + (iters - 1) * (f2 + N * c2) + (f3 + N * c3)
+    rate = N * (iters + 1) / t_step
+    desc = (f"fixed cost per pass + packets/s from a small and a large sample of each kind of pass: "
+            f"cold-start Lucy iteration {f1:.2f} s + {1 / c1:.3g} packets/s ({n1} packets, {t1:.1f} s), "
+            f"Lucy iteration at the oracle's own T after it {f2:.2f} s + {1 / c2:.3g} packets/s ({n2}, {t2:.1f} s), "
+            f"imaging pass {f3:.2f} s + {1 / c3:.3g} packets/s ({n3}, {t3:.1f} s); the step is 1 + {iters - 1} + 1 "
+            f"passes of {N:.3g} packets")
+    return rate, cores, desc
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
-    times, rates = [], []
-    seconds = max(2.0, min(args.cpu_seconds, 200.0 / max(1, args.steps + args.warmup)))
+    wl = workload(args.packets, 0, args.workload)
+    times, rates, desc, cores = [], [], "", 1
+    seconds = max(0.3, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    cpu_oracle_rate(wl, args.iters, seconds)         # the cost model (fixed costs per kind of pass)
     for i in range(args.warmup + args.steps):
-        r, cores, n, dt = cpu_oracle_rate(args, seconds)
+        t0 = time.perf_counter()
+        r, cores, desc = cpu_oracle_rate(wl, args.iters, seconds, refresh=True)
         if i >= args.warmup:
             rates.append(r)
-            times.append(dt)
+            times.append(time.perf_counter() - t0)
     value = statistics.median(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} packets of one Lucy iteration of the disk per step"},
+                             "sample": "per step: " + desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm
+def l2_peaks(torch):
+    """L2-resident peaks measured in this process with CUDA events: the best copy rate over buffer
+    pairs of 2-24 MiB (both buffers in L2; read + write bytes) and FP64 atomic adds (index_add_) of
+    2^26 values into 25,600 accumulators (the disk's cell count; the index and value streams come
+    from HBM)."""
+    dev = "cuda"
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l2_gbs, l2_size = 0.0, 0
+    for mib in (2, 4, 8, 16, 24):
+        a = torch.empty(mib * 1024 * 1024 // 4, dtype=torch.float32, device=dev).uniform_()
+        b = torch.empty_like(a)
+        for _ in range(5):
+            b.copy_(a)
+        reps = max(20, 1200 // mib)
+        for _ in range(3):
+            ev0.record()
+            for _ in range(reps):
+                b.copy_(a)
+            ev1.record()
+            torch.cuda.synchronize()
+            gbs = 2 * a.numel() * 4 * reps / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+            if gbs > l2_gbs:
+                l2_gbs, l2_size = gbs, mib
+        del a, b
+    n = 1 << 26
+    acc = torch.zeros(25600, dtype=torch.float64, device=dev)
+    idx = torch.randint(0, 25600, (n,), device=dev)
+    val = torch.ones(n, dtype=torch.float64, device=dev)
+    acc.index_add_(0, idx, val)
+    best = float("inf")
+    for _ in range(5):
+        ev0.record()
+        acc.index_add_(0, idx, val)
+        ev1.record()
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    atom = n / (best * 1e-3)
+    del acc, idx, val
+    return {"l2_copy_gbs": l2_gbs, "l2_fp64_atomics_per_s": atom,
+            "how": f"CUDA events: best copy rate over 2-24 MiB buffer pairs (best at {l2_size} MiB); index_add_ of "
+                   "2^26 FP64 values into 25,600 accumulators (best of 5)"}
+
+
+class Runner:
+    """One model in one libhrt context and the step that `bench.py` times on it."""
+
+    def __init__(self, hrt, torch, wl, local, stream, kernel, iters):
+        self.hrt, self.torch, self.wl, self.iters = hrt, torch, wl, iters
+        self.m = hrt.Model(wl, device=local, stream=stream)
+        self.L = hrt.load()
+        self.kern = hrt.HRT_KERNEL_EVENT if kernel == "event" else hrt.HRT_KERNEL_PLAIN
+        self.nc = self.m.ncells
+        self.T0 = torch.full((self.nc,), 10.0, dtype=torch.float64, device="cuda")
+
+    def solve(self, stats, pda_min=0, peel=True):
+        """One step on device-resident inputs: Lucy iterations from the cold start, then the
+        imaging pass."""
+        hrt, m = self.hrt, self.m
+        hrt.check(m.ctx, self.L.hrt_set_temperature_device(m.ctx, self.T0.data_ptr(), self.nc))
+        hrt.check(m.ctx, self.L.hrt_set_iteration(m.ctx, 0))
+        for _ in range(self.iters):
+            stats.append(m.run_iteration(n_packets=self.wl.n_packets, kernel=self.kern, pda_min_visits=pda_min))
+        if peel:
+            stats.append(m.run_iteration(n_packets=self.wl.n_packets, kernel=self.kern, peel=1, update_temperature=0))
+
+    def timed_steps(self, steps, warmup, stream, barrier, flush):
+        torch = self.torch
+        for _ in range(warmup):
+            self.solve([])
+        barrier()
+        ms, stats = [], []
+        for _ in range(steps):
+            flush.zero_()
+            barrier()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            st = []
+            ev0.record(stream)
+            self.solve(st)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            stats.append(st)
+        return ms, stats
+
+    def e2e_steps(self, steps, barrier, flush):
+        """The step through the C ABI with pinned host buffers, copies inside the timed region."""
+        import numpy as np
+        torch, hrt, m, L, nc = self.torch, self.hrt, self.m, self.L, self.nc
+        rho_h = torch.from_numpy(np.ascontiguousarray(self.wl.rho.reshape(-1), dtype=np.float32)).pin_memory()
+        T0_h = torch.full((nc,), 10.0, dtype=torch.float64).pin_memory()
+        T_out = torch.empty(nc, dtype=torch.float64).pin_memory()
+        sed_out = torch.empty(m.nobs * self.wl.nsed, dtype=torch.float64).pin_memory()
+        nimg = len(self.wl.img_lam_um) if self.wl.img_nx > 0 else 0
+        img_out = torch.empty(max(1, m.nobs * nimg * self.wl.img_nx * self.wl.img_ny), dtype=torch.float64).pin_memory()
+        out = []
+        for _ in range(max(1, steps)):
+            flush.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            hrt.check(m.ctx, L.hrt_set_density(m.ctx, rho_h.data_ptr(), nc))
+            hrt.check(m.ctx, L.hrt_set_temperature(m.ctx, T0_h.data_ptr(), nc))
+            hrt.check(m.ctx, L.hrt_set_iteration(m.ctx, 0))
+            for _ in range(self.iters):
+                m.run_iteration(n_packets=self.wl.n_packets, kernel=self.kern)
+            m.run_iteration(n_packets=self.wl.n_packets, kernel=self.kern, peel=1, update_temperature=0)
+            hrt.check(m.ctx, L.hrt_get_temperature(m.ctx, T_out.data_ptr(), nc))
+            hrt.check(m.ctx, L.hrt_get_sed(m.ctx, sed_out.data_ptr(), sed_out.numel()))
+            if nimg:
+                hrt.check(m.ctx, L.hrt_get_image(m.ctx, img_out.data_ptr(), img_out.numel()))
+            torch.cuda.synchronize()
+            out.append(1e3 * (time.perf_counter() - t0))
+        h2d = int(rho_h.numel() * 4 + T0_h.numel() * 8)
+        d2h = int(T_out.numel() * 8 + sed_out.numel() * 8 + (img_out.numel() * 8 if nimg else 0))
+        return out, h2d, d2h
+
+    def close(self):
+        self.m.close()
+
+
+def convergence_fields(stats_steps, iters):
+    qs = [[s["Q"] for s in st[:iters]] for st in stats_steps]
+    ms = [[s["ms_total"] for s in st[:iters]] for st in stats_steps]
+    lit = [converged_at(q, m, 1.02) for q, m in zip(qs, ms)]
+    dlt = [converged_at(q, m, 2.0, 1.02) for q, m in zip(qs, ms)]
+
+    def med(v):
+        v = [x for x in v if x is not None]
+        return statistics.median(v) if v else None
+    return {"time_to_converged_ms": med([t for _, t in lit]),
+            "iterations_to_converged": med([i for i, _ in lit]),
+            "time_to_converged_delta_ms": med([t for _, t in dlt]),
+            "iterations_to_converged_delta": med([i for i, _ in dlt]),
+            "q99_history": [round(q, 5) for q in qs[-1]]}
+
+
+def lucy_roofline(last, iters, peak, src):
+    """Roofline of the Lucy propagation kernel: mean over the step's Lucy launches."""
+    lucy = last[:iters]
+    byts = statistics.mean(B_CROSS * s["n_crossings"] + B_REEMIT * s["n_absorb"] for s in lucy)
+    kms = statistics.mean(s["ms_propagate"] for s in lucy)
+    cross = statistics.mean(s["n_crossings"] for s in lucy)
+    achieved = byts / (kms * 1e-3) / 1e9
+    traffic = TRAFFIC_PER_CROSSING * cross if TRAFFIC_PER_CROSSING else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)", "peak_source": src,
+            "kernel": "k_event (Lucy iteration)", "kernel_ms_per_launch": kms,
+            "algorithmic_bytes_per_launch": byts, "crossings_per_launch": cross,
+            "crossings_per_s": cross / (kms * 1e-3)}
+
+
+def disk_line(hrt, torch, local, stream, barrier, flush, steps, warmup, pda_min, l2):
+    """The L2-resident flared disk (1e7 packets x 10 iterations + peel-off pass)."""
+    wl = workload(10_000_000, 0, "disk")
+    r = Runner(hrt, torch, wl, local, stream, "event", 10)
+    ms, stats = r.timed_steps(steps, warmup, stream, barrier, flush)
+    last = stats[-1]
+    packets_step = wl.n_packets * 11
+    lucy = last[:10]
+    kms = statistics.mean(s["ms_propagate"] for s in lucy)
+    byts = statistics.mean(B_CROSS * s["n_crossings"] + B_REEMIT * s["n_absorb"] for s in lucy)
+    atoms = statistics.mean(s["n_crossings"] for s in lucy)       # at most one FP64 atomic per crossing
+    achieved = byts / (kms * 1e-3) / 1e9
+    out = {"workload": describe("disk", wl.n_packets, 10), "packets_per_s": packets_step * steps / (sum(ms) * 1e-3),
+           "ms_per_step": statistics.mean(ms), "steps": steps,
+           "roofline": {"bound": "l2", "achieved": achieved, "peak": l2["l2_copy_gbs"], "unit": "GB/s",
+                        "frac": achieved / l2["l2_copy_gbs"], "peak_source": "measured in this run (L2 copy)",
+                        "kernel": "k_event (Lucy iteration)", "kernel_ms_per_launch": kms,
+                        "fp64_atomic_bound_per_s": atoms / (kms * 1e-3),
+                        "fp64_atomic_frac": atoms / (kms * 1e-3) / l2["l2_fp64_atomics_per_s"]}}
+    out.update(convergence_fields(stats, 10))
+    if pda_min > 0:
+        # time to the criterion with the partial diffusion approximation (App. A) for the cells
+        # entered by fewer than pda_min packets (not part of the timed throughput steps)
+        st = []
+        r.solve(st, pda_min=pda_min, peel=False)
+        q = [s["Q"] for s in st]
+        it, t = converged_at(q, [s["ms_total"] for s in st], 1.02)
+        out["pda"] = {"min_visits": pda_min, "cells": st[-1]["n_pda"], "q99_history": [round(x, 5) for x in q],
+                      "iterations_to_converged": it, "time_to_converged_ms": t}
+    r.close()
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -210,7 +498,6 @@ def main():
     if args.rows:
         return rows_bench(local)
 
-    import numpy as np
     import torch
     from paper_1112_1071_gb300 import hrt
 
@@ -226,142 +513,63 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    wl = workload(args.packets, rank)
-    m = hrt.Model(wl, device=local, stream=stream)
-    L = hrt.load()
-    kern = hrt.HRT_KERNEL_EVENT if args.kernel == "event" else hrt.HRT_KERNEL_PLAIN
-    nc = m.ncells
-    T0 = torch.full((nc,), 10.0, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-
-    def solve(stats):
-        """One step: Lucy iterations from the cold start, then the peel-off pass."""
-        hrt.check(m.ctx, L.hrt_set_temperature_device(m.ctx, T0.data_ptr(), nc))
-        hrt.check(m.ctx, L.hrt_set_iteration(m.ctx, 0))
-        for _ in range(args.iters):
-            stats.append(m.run_iteration(n_packets=args.packets, kernel=kern))
-        stats.append(m.run_iteration(n_packets=args.packets, kernel=kern, peel=1, update_temperature=0))
-
-    # warm-up
-    for _ in range(args.warmup):
-        solve([])
-    barrier()
+    wl = workload(args.packets, rank, args.workload)
+    run = Runner(hrt, torch, wl, local, stream, args.kernel, args.iters)
     clocks = Clocks(local)
     clocks.start()
-    step_ms, all_stats, conv = [], [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        barrier()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        st = []
-        ev0.record(stream)
-        solve(st)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        all_stats.append(st)
-        # time to the 2% criterion: iterations until Q_99(delta T) < 1.02
-        t, it_conv = 0.0, None
-        for i, s in enumerate(st[:-1]):
-            t += s["ms_total"]
-            if s["converged"] and i > 0:
-                it_conv = i + 1
-                break
-        conv.append((it_conv, t if it_conv else None))
-    # time to the 2% criterion with the partial diffusion approximation (App. A) for the cells
-    # entered by fewer than --pda-min packets (not part of the timed throughput steps)
-    conv_pda, pda_q, pda_cells = [], [], 0
-    if args.pda_min > 0:
-        for _ in range(args.steps):
-            hrt.check(m.ctx, L.hrt_set_temperature_device(m.ctx, T0.data_ptr(), nc))
-            hrt.check(m.ctx, L.hrt_set_iteration(m.ctx, 0))
-            t, it_conv, qh = 0.0, None, []
-            for i in range(args.iters):
-                s = m.run_iteration(n_packets=args.packets, kernel=kern, pda_min_visits=args.pda_min)
-                t += s["ms_total"]
-                qh.append(round(s["Q"], 5))
-                pda_cells = s["n_pda"]
-                if s["converged"] and i > 0:
-                    it_conv = i + 1
-                    break
-            conv_pda.append((it_conv, t if it_conv else None))
-            pda_q = qh
+    step_ms, all_stats = run.timed_steps(args.steps, args.warmup, stream, barrier, flush)
     barrier()
     clk = clocks.stop()
-
-    # ---- end-to-end through the C ABI with host buffers
-    rho_h = torch.from_numpy(np.ascontiguousarray(wl.rho.reshape(-1), dtype=np.float32)).pin_memory()
-    T0_h = torch.full((nc,), 10.0, dtype=torch.float64).pin_memory()
-    T_out = torch.empty(nc, dtype=torch.float64).pin_memory()
-    sed_out = torch.empty(m.nobs * wl.nsed, dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    for k in range(max(1, args.steps)):
-        flush.zero_()
-        barrier()
-        t0 = time.perf_counter()
-        hrt.check(m.ctx, L.hrt_set_density(m.ctx, rho_h.data_ptr(), nc))
-        hrt.check(m.ctx, L.hrt_set_temperature(m.ctx, T0_h.data_ptr(), nc))
-        hrt.check(m.ctx, L.hrt_set_iteration(m.ctx, 0))
-        for _ in range(args.iters):
-            m.run_iteration(n_packets=args.packets, kernel=kern)
-        m.run_iteration(n_packets=args.packets, kernel=kern, peel=1, update_temperature=0)
-        hrt.check(m.ctx, L.hrt_get_temperature(m.ctx, T_out.data_ptr(), nc))
-        hrt.check(m.ctx, L.hrt_get_sed(m.ctx, sed_out.data_ptr(), sed_out.numel()))
-        torch.cuda.synchronize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms, h2d, d2h = run.e2e_steps(min(args.steps, 5), barrier, flush)
     barrier()
+    launches = sum(s["kernel_launches"] for st in all_stats for s in st)
+    run.close()
 
     packets_step = args.packets * (args.iters + 1)
-    ms = statistics.mean(step_ms)
     value, e2e_value, _, _ = job_throughput(sum(step_ms), statistics.mean(e2e_ms), world, packets_step, args.steps,
                                             dist, "cuda")
-
-    # ---- roofline of the propagation kernel (Lucy iterations and the peel-off pass)
-    last = all_stats[-1]
-    byts = sum(B_CROSS * s["n_crossings"] + B_PEEL * s["n_peel_crossings"] + B_REEMIT * (s["n_absorb"]) for s in last)
-    kms = sum(s["ms_propagate"] for s in last)
-    peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         peak, src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         peak, src = 6800.0, "fallback"
-    achieved = byts / (kms * 1e-3) / 1e9
-    launches = sum(s["kernel_launches"] for st in all_stats for s in st)
-    its, tconv = zip(*conv)
-    done = [t for t in tconv if t is not None]
+    last = all_stats[-1]
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(args, world),
-            "time_to_converged_ms": statistics.median(done) if done else None,
-            "q99_history": [round(s["Q"], 5) for s in last[:-1]],
-            "iterations_to_converged": statistics.median([i for i in its if i]) if any(its) else None,
-            "time_to_converged_pda_ms": statistics.median([t for _, t in conv_pda if t is not None])
-            if any(t is not None for _, t in conv_pda) else None,
-            "pda": {"min_visits": args.pda_min, "cells": pda_cells, "q99_history": pda_q,
-                    "iterations_to_converged": statistics.median([i for i, _ in conv_pda if i])
-                    if any(i for i, _ in conv_pda) else None} if args.pda_min > 0 else None,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": config(args, world)}
+        line.update(convergence_fields(all_stats, args.iters))
+        line.update({
+            "lucy_ms_per_iteration": statistics.mean(s["ms_total"] for s in last[:args.iters]),
+            "imaging_ms": last[-1]["ms_total"],
             "crossings_per_step": sum(s["n_crossings"] for s in last),
             "peel_crossings_per_step": sum(s["n_peel_crossings"] for s in last),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH if kern == hrt.HRT_KERNEL_EVENT else None,
-                         "traffic_unit": "bytes per launch (ncu)", "peak_source": src,
-                         "kernel": "k_event + k_peel_rays (propagation)" if kern == hrt.HRT_KERNEL_EVENT else "k_plain",
-                         "kernel_ms_per_step": kms, "algorithmic_bytes_per_step": byts},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rho_h.numel() * 4 + T0_h.numel() * 8),
-                    "d2h_bytes_per_step": int(T_out.numel() * 8 + sed_out.numel() * 8)},
+            "roofline": lucy_roofline(last, args.iters, peak, src),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
-        }
+        })
+    if not args.no_extras and rank == 0:
+        # the plain-GPU comparison: the same step with one thread per packet history
+        if args.kernel == "event":
+            pr = Runner(hrt, torch, wl, local, stream, "plain", args.iters)
+            pms, _ = pr.timed_steps(1, 1, stream, barrier, flush)
+            pr.close()
+            line["plain_gpu"] = {"value": packets_step / (pms[0] * 1e-3), "unit": UNIT, "ms_per_step": pms[0],
+                                 "kernel": "k_plain (one thread per history)", "steps": 1, "warmup": 1}
+        if args.workload == "cloud":
+            l2 = l2_peaks(torch)
+            line["l2_peaks"] = l2
+            line["flared_disk"] = disk_line(hrt, torch, local, stream, barrier, flush, 3, 2, args.pda_min, l2)
+    if line is not None:
         if not args.no_cpu_baseline:
-            r, cores, n, dt = cpu_oracle_rate(args, args.cpu_seconds)
-            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": f"{n} packets of one Lucy iteration of the disk ({dt:.1f} s)"}
+            r, cores, desc = cpu_oracle_rate(wl, args.iters, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
         print(json.dumps(line), flush=True)
-    m.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
