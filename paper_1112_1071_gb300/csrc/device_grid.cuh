@@ -89,6 +89,50 @@ __device__ __forceinline__ bool cart_step(const DevGrid& g, Ray& r, float l, int
     }
 }
 
+// The same walk with the next wall of every axis (the wall the ray moves towards) held by the
+// caller in wn: cart_next_walls loads them when a ray starts, cart_exit_w equals cart_exit, and
+// cart_step_w equals cart_step without branching on the crossed axis, loading only that axis's
+// next wall -- one table load per crossing instead of four, the same FP32 operations.
+__device__ __forceinline__ float3 cart_next_walls(const DevGrid& g, const Ray& r) {
+    return make_float3(__ldg(g.w1 + r.i + (r.u.x > 0.f)), __ldg(g.w2 + r.j + (r.u.y > 0.f)),
+                       __ldg(g.w3 + r.k + (r.u.z > 0.f)));
+}
+
+__device__ __forceinline__ float cart_exit_w(const Ray& r, float3 wn, int& axis) {
+    const float dx = r.u.x != 0.f ? fmaxf((wn.x - r.p.x) * r.inv.x, 0.f) : F_INF;
+    const float dy = r.u.y != 0.f ? fmaxf((wn.y - r.p.y) * r.inv.y, 0.f) : F_INF;
+    const float dz = r.u.z != 0.f ? fmaxf((wn.z - r.p.z) * r.inv.z, 0.f) : F_INF;
+    // ties go to the lowest axis
+    const bool bx = dx <= dy && dx <= dz;
+    const bool by = !bx && dy <= dz;
+    axis = bx ? 0 : (by ? 1 : 2);
+    return bx ? dx : (by ? dy : dz);
+}
+
+__device__ __forceinline__ bool cart_step_w(const DevGrid& g, Ray& r, float3& wn, float l, int axis) {
+    const bool ax = axis == 0, ay = axis == 1;
+    const bool az = !ax && !ay;
+    r.p.x = ax ? wn.x : r.p.x + l * r.u.x;
+    r.p.y = ay ? wn.y : r.p.y + l * r.u.y;
+    r.p.z = az ? wn.z : r.p.z + l * r.u.z;
+    const float ua = ax ? r.u.x : (ay ? r.u.y : r.u.z);
+    const int up = ua > 0.f;
+    const int s = up ? 1 : -1;
+    r.i += ax ? s : 0;
+    r.j += ay ? s : 0;
+    r.k += az ? s : 0;
+    r.ci += ax ? s : (ay ? s * g.n1 : s * g.n1 * g.n2);
+    const bool out = (unsigned)r.i >= (unsigned)g.n1 || (unsigned)r.j >= (unsigned)g.n2 || (unsigned)r.k >= (unsigned)g.n3;
+    if (!out) {
+        const float* w = ax ? g.w1 : (ay ? g.w2 : g.w3);
+        const float v = __ldg(w + (ax ? r.i : (ay ? r.j : r.k)) + up);
+        wn.x = ax ? v : wn.x;
+        wn.y = ay ? v : wn.y;
+        wn.z = az ? v : wn.z;
+    }
+    return out;
+}
+
 __device__ __forceinline__ bool cart_locate(const DevGrid& g, Ray& r) {
     r.i = locate_axis(g.w1, g.n1, r.p.x, r.u.x);
     r.j = locate_axis(g.w2, g.n2, r.p.y, r.u.y);

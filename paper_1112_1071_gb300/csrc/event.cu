@@ -27,43 +27,6 @@ namespace hrt {
 enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE, M_MRW };
 
 
-// Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
-// With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
-// group adds its sum with one FP64 atomic.  Each flushed run is one packet entry of the cell,
-// counted into `visits` when the diffusion approximation needs it.
-template <bool WAGG>
-__device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, bool flushing, int32_t ci, float v) {
-    if constexpr (WAGG) {
-        const unsigned lane = threadIdx.x & 31u;
-        const int key = flushing ? ci : -1 - (int)lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (!flushing) return;
-        if (__popc(peers) == 1) {
-            atomicAdd(acc + ci, widen(v));
-            if (visits) atomicAdd(visits + ci, 1u);
-            return;
-        }
-        float sum = 0.f;
-        for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
-        if (lane == (unsigned)(__ffs(peers) - 1)) {
-            atomicAdd(acc + ci, widen(sum));
-            if (visits) atomicAdd(visits + ci, (uint32_t)__popc(peers));
-        }
-    } else {
-        if (flushing) {
-            atomicAdd(acc + ci, widen(v));
-            if (visits) atomicAdd(visits + ci, 1u);
-        }
-    }
-}
-
-// End of a lane's run outside the walk step (packet end, watchdog, kernel end).
-__device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v) {
-    if (ci < 0) return;
-    if (v != 0.f) atomicAdd(t.acc + ci, widen(v));
-    if (t.visits) atomicAdd(t.visits + ci, 1u);
-}
-
 // The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
 // `need` (ballot) lanes want a packet and returns this lane's packet id, or -1 when none is left.
 template <int G, bool WAGG, bool PEEL, bool MRW, class Fetch>
@@ -86,6 +49,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     int zero_run = 0;
     unsigned ray_steps = 0;    // crossings of the current ray since it started or last interacted
     bool aborted = false;
+    // the walk's look-ahead: the density of the current cell, loaded one crossing ahead (when the
+    // ray entered the cell), and (Cartesian) the next wall of every axis; `fresh` marks a ray that
+    // starts (or starts again) and needs both loaded
+    bool fresh = true;
+    float rho_nx = 0.f;
+    float3 wn = make_float3(0.f, 0.f, 0.f);
 
     auto start_walk = [&]() {
         if constexpr (MRW) {
@@ -97,6 +66,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         tau = -logf(pk.rng.next());
         ray_steps = 0;
         zero_run = 0;
+        fresh = true;
         mode = M_WALK;
     };
     // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction);
@@ -113,6 +83,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         tau = 0.f;
         ray_steps = 0;
         zero_run = 0;
+        fresh = true;
         mode = M_PEEL;
         if (prelocate && !grid_locate<G>(g, pk.r)) mode = M_PEEL_DONE;
     };
@@ -216,6 +187,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             tau = -logf(pk.rng.next());
             ray_steps = 0;
             zero_run = 0;
+            fresh = true;
             mode = M_WALK;
             return;
         }
@@ -314,9 +286,16 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             int32_t fci = 0;
             float fval = 0.f;
             if (mode == M_WALK || mode == M_PEEL) {
-                int axis, dir;
-                const float l = cell_exit<G>(g, pk.r, axis, dir);
-                const float rho = __ldg(g.rhoL + pk.r.ci);
+                int axis, dir = 0;
+                float l;
+                if constexpr (G == GRID_CARTESIAN) {
+                    if (fresh) wn = cart_next_walls(g, pk.r);
+                    l = cart_exit_w(pk.r, wn, axis);
+                } else {
+                    l = cell_exit<G>(g, pk.r, axis, dir);
+                }
+                const float rho = fresh ? __ldg(g.rhoL + pk.r.ci) : rho_nx;
+                fresh = false;
                 const float k = rho * pk.dust.chi;
                 bool stop = false;
                 if (!PEEL || mode == M_WALK) {
@@ -355,7 +334,11 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     if (tau > PEEL_TAU_STOP) stop = true, mode = M_PEEL_DONE;
                 }
                 if (!stop) {
-                    if (cell_step<G>(g, pk.r, l, axis, dir)) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
+                    bool out;
+                    if constexpr (G == GRID_CARTESIAN) out = cart_step_w(g, pk.r, wn, l, axis);
+                    else out = cell_step<G>(g, pk.r, l, axis, dir);
+                    if (out) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
+                    else rho_nx = __ldg(g.rhoL + pk.r.ci);      // the next crossing's density, ahead of use
                     if constexpr (G != GRID_CARTESIAN) {
                         if (!tiny_step(pk.r, l)) zero_run = 0;
                         else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
@@ -408,11 +391,16 @@ __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSo
 }
 
 // MRW = modified random walk compiled in (runs with mrw_gamma > 0; 3 blocks per SM only)
+// WAGG (deposits of a warp's lanes grouped by cell before the atomic) on Cartesian grids only:
+// measured on GB300, it saves 10 % of a Lucy iteration on the 256^3 cloud (large accumulator
+// array beyond L2, fewer reductions) and costs 13 % on the disk (accumulators in L2, where the
+// grouping's match.any per crossing outweighs the atomics it saves).
 template <int G, bool PEEL>
 static cudaError_t launch_event_shape(const PropagateJob& j, const Launch& l, int bps, cudaStream_t s) {
-    if (j.args.mrw_gamma > 0.f) return launch_persistent(k_event<G, true, 3, PEEL, true>, j, l, s);
-    if (bps >= 3) return launch_persistent(k_event<G, true, 3, PEEL, false>, j, l, s);
-    return launch_persistent(k_event<G, true, 2, PEEL, false>, j, l, s);
+    constexpr bool WAGG = G == GRID_CARTESIAN;
+    if (j.args.mrw_gamma > 0.f) return launch_persistent(k_event<G, WAGG, 3, PEEL, true>, j, l, s);
+    if (bps >= 3) return launch_persistent(k_event<G, WAGG, 3, PEEL, false>, j, l, s);
+    return launch_persistent(k_event<G, WAGG, 2, PEEL, false>, j, l, s);
 }
 
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched) {
@@ -421,15 +409,16 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     ll.block = 256;
     PropagateJob j = job;
     const bool peel = job.args.peel != 0;
-    // default shapes (measured on GB300): 3 blocks of 256 per SM (80 registers); warps stay in
-    // the walk phase while at least 24 lanes walk (curvilinear grids; Cartesian runs of >= 4M
-    // packets), 12 for small Cartesian runs whose tail dominates
+    // default shapes (measured on GB300): Lucy iterations at 3 blocks of 256 per SM (80
+    // registers), imaging passes at 2 (128 registers: the peel-off code spills at 80); warps stay
+    // in the walk phase while at least 24 lanes walk on curvilinear grids, 20 on Cartesian runs of
+    // >= 4M packets, 12 for small Cartesian runs whose tail dominates
     int rg_default = DEFAULT_REGROUP;
     if (job.grid.type != GRID_CARTESIAN) rg_default = 24;
-    else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 24;
+    else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 2 : 3);
     cudaError_t e;
     if (job.grid.type == GRID_CARTESIAN)
         e = peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)

@@ -73,11 +73,13 @@ enum PeelKind : int32_t { PEEL_ISO = 0, PEEL_HG = 1 };
 // relocate, the starting cell is found along each observer direction (emission from a point
 // source, which may sit on walls or in the spherical hole); otherwise the packet's cell is used.
 // With col (emission from a point source whose columns were precomputed), tau_obs = chi col[ob]:
-// every packet of that source peels along the same rays, so they are walked once per pass.
+// every packet of that source peels along the same rays, so they are walked once per pass.  A ray
+// stops once its optical depth passes tau_stop (its weight is then below exp(-tau_stop)).
 template <int G>
 __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, const RunArgs& a,
                            const Tallies& t, double* sed_s, const Ray& at, float3 uin, int kind, bool relocate,
-                           float chi, int sbin, LocalCounters& lc, const float* col = nullptr) {
+                           float chi, int sbin, LocalCounters& lc, const float* col = nullptr,
+                           float tau_stop = F_INF) {
     if (sbin < 0) return;
     for (int ob = 0; ob < o.nobs; ++ob) {
         const float3 n = make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2));
@@ -89,7 +91,7 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
         if (col) tau = chi * fmaxf(__ldg(col + ob), 0.f);
         else {
             if (relocate) inside = grid_locate<G>(g, pr);
-            if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], F_INF);
+            if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], tau_stop);
         }
         const double w = a.eps * (double)(prob * expf(-tau));
         if (sed_s) atomicAdd(sed_s + ob * o.nsed + sbin, w);

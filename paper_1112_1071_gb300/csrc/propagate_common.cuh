@@ -46,6 +46,45 @@ __device__ __forceinline__ bool past_deadline(const RunArgs& a, const Tallies& t
     return false;
 }
 
+// Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
+// With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
+// group adds its sum (formed in FP64) with one FP64 atomic.  Each flushed run is one packet entry of the cell,
+// counted into `visits` when the diffusion approximation needs it.
+template <bool WAGG>
+__device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, bool flushing, int32_t ci, float v) {
+    if constexpr (WAGG) {
+        const unsigned lane = threadIdx.x & 31u;
+        const int key = flushing ? ci : -1 - (int)lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (!flushing) return;
+        if (__popc(peers) == 1) {
+            atomicAdd(acc + ci, widen(v));
+            if (visits) atomicAdd(visits + ci, 1u);
+            return;
+        }
+        // the group's sum in FP64 (exact widening, then FP64 adds): the result does not depend
+        // on which packets happen to share a warp step, to FP64 rounding
+        double sum = 0.0;
+        for (unsigned m = peers; m; m &= m - 1) sum += widen(__shfl_sync(peers, v, __ffs(m) - 1));
+        if (lane == (unsigned)(__ffs(peers) - 1)) {
+            atomicAdd(acc + ci, sum);
+            if (visits) atomicAdd(visits + ci, (uint32_t)__popc(peers));
+        }
+    } else {
+        if (flushing) {
+            atomicAdd(acc + ci, widen(v));
+            if (visits) atomicAdd(visits + ci, 1u);
+        }
+    }
+}
+
+// End of a lane's run outside the walk step (packet end, watchdog, kernel end).
+__device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v) {
+    if (ci < 0) return;
+    if (v != 0.f) atomicAdd(t.acc + ci, widen(v));
+    if (t.visits) atomicAdd(t.visits + ci, 1u);
+}
+
 // Optical depth beyond which a peel-off ray stops: exp(-40) = 4e-18 of its weight remains.
 constexpr float PEEL_TAU_STOP = 40.f;
 
