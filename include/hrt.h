@@ -140,7 +140,16 @@ int hrt_set_peeloff(hrt_ctx* ctx, int nobs, const double* incl, const double* az
 
 /* ------------------------------------------------------------------ iteration (Sects. 2.2-2.4) */
 
-typedef enum { HRT_KERNEL_EVENT = 0, HRT_KERNEL_PLAIN = 1 } hrt_kernel;
+/* Propagation kernels; all three draw packet p from the same Philox stream in the same order, so
+ * their histories are the same.  HRT_KERNEL_EVENT: persistent event-based propagation in which
+ * each warp's lanes walk together and handle their events in a short event phase (the default,
+ * and the fastest on the benchmark workloads).  HRT_KERNEL_PLAIN: one thread per packet
+ * history, the plain-GPU comparison.  HRT_KERNEL_REGROUP: the event-based form with the live
+ * packets regrouped by state across the warps of a block -- walker warps hand stopped packets to
+ * a service warp through shared-memory queues, and it runs each kind of event (scattering,
+ * absorption and re-emission, new packets) in same-state batches; modified-random-walk runs
+ * use HRT_KERNEL_EVENT instead. */
+typedef enum { HRT_KERNEL_EVENT = 0, HRT_KERNEL_PLAIN = 1, HRT_KERNEL_REGROUP = 2 } hrt_kernel;
 
 typedef struct {
     int64_t max_interactions;    /* per packet; a packet beyond it is killed and its energy tallied */
@@ -337,6 +346,9 @@ int hrt_get_visits(hrt_ctx* ctx, uint32_t* out, int64_t n);
  * Output: y = (log10 T[K] - 1.5) / 0.5.  D, H, W must be multiples of 2^L. */
 typedef struct hrt_net hrt_net;
 int hrt_net_create(hrt_net** out, int device, int base_channels, int levels, uint64_t seed, void* stream);
+/* The same network with the width of every level given: widths[0..levels] (multiples of 32, at
+ * most 512), e.g. {32, 64, 192} at 2 levels (2.19M parameters).  HRT_EINVAL otherwise. */
+int hrt_net_create_widths(hrt_net** out, int device, const int* widths, int levels, uint64_t seed, void* stream);
 int hrt_net_destroy(hrt_net* net);
 /* Parameters in packed order: per conv layer W[27][Cin][Cout] (tap = 9 dz + 3 dy + dx) then
  * b[Cout]; then the head w[c], b[1].  */

@@ -748,7 +748,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
     if (!(P.mrw_gamma >= 0) || !std::isfinite(P.mrw_gamma))
         return ctx->fail(HRT_EINVAL, "mrw_gamma must be finite and >= 0");
     if (P.peel_queue_events < 0) return ctx->fail(HRT_EINVAL, "peel_queue_events must be >= 0");
-    if (P.kernel != HRT_KERNEL_EVENT && P.kernel != HRT_KERNEL_PLAIN) return ctx->fail(HRT_EINVAL, "unknown kernel");
+    if (P.kernel != HRT_KERNEL_EVENT && P.kernel != HRT_KERNEL_PLAIN && P.kernel != HRT_KERNEL_REGROUP)
+        return ctx->fail(HRT_EINVAL, "unknown kernel");
     if (P.quantity != 0 && P.quantity != 1) return ctx->fail(HRT_EINVAL, "quantity must be 0 (T) or 1 (Adot)");
     if (P.block_size != 0 && P.block_size != 256)
         return ctx->fail(HRT_EINVAL, "block_size must be 0 or 256 (the kernels are compiled for 256 threads)");
@@ -868,7 +869,8 @@ int hrt_run_iteration(hrt_ctx* ctx, int64_t n_packets, const hrt_run_params* par
         job.args.peel_cap = cap;
     }
     cudaError_t e = P.kernel == HRT_KERNEL_PLAIN ? launch_propagate_plain(job, L, s, &launched)
-                                                 : launch_propagate_event(job, L, s, &launched);
+                    : (P.kernel == HRT_KERNEL_REGROUP && regroup_supported(job)) ? launch_propagate_regroup(job, L, s, &launched)
+                                                                            : launch_propagate_event(job, L, s, &launched);
     CK(e, "propagate");
     if (job.args.peel_q) {
         const size_t nk = (size_t)nc + 1;

@@ -34,6 +34,10 @@ cudaError_t launch_propagate_plain(const PropagateJob& job, const Launch& l, cud
 cudaError_t launch_source_columns(const DevGrid& g, const DevSources& src, const DevObs& o, float* col,
                                   cudaStream_t s);
 cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
+// regroup.cu: the event kernel with packets regrouped by state across a block's warps (not for
+// modified-random-walk runs; see regroup_supported)
+bool regroup_supported(const PropagateJob& job);
+cudaError_t launch_propagate_regroup(const PropagateJob& job, const Launch& l, cudaStream_t s, int* launched);
 // peel.cu: the peel pass of an imaging pass over the events the event kernel queued in
 // job.args.peel_q; hist [ncells + 1], sums [(ncells + 1024) / 1024], order [peel_cap] scratch
 cudaError_t launch_peel_pass(const PropagateJob& job, uint32_t* hist, uint32_t* sums, uint32_t* order, cudaStream_t s,

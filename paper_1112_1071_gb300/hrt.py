@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhrt.so")
 
 HRT_OK, HRT_EINVAL, HRT_ENOMEM, HRT_ESTATE, HRT_ECUDA, HRT_ETIMEDOUT, HRT_ERANGE = 0, -1, -2, -3, -4, -5, -6
-HRT_KERNEL_EVENT, HRT_KERNEL_PLAIN = 0, 1
+HRT_KERNEL_EVENT, HRT_KERNEL_PLAIN, HRT_KERNEL_REGROUP = 0, 1, 2
 _STATUS = {0: "HRT_OK", -1: "HRT_EINVAL", -2: "HRT_ENOMEM", -3: "HRT_ESTATE", -4: "HRT_ECUDA",
            -5: "HRT_ETIMEDOUT", -6: "HRT_ERANGE"}
 
@@ -116,6 +116,7 @@ _SIGS = {
     "hrt_get_visits": (C.c_int, [_vp, _vp, _i64]),
     "hrt_quantile_ratio_noalloc": (C.c_int, [_i64, _vp, _vp, _vp, C.c_double, _vp, _vp]),
     "hrt_net_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_uint64, _vp]),
+    "hrt_net_create_widths": (C.c_int, [C.POINTER(_vp), C.c_int, _vp, C.c_int, C.c_uint64, _vp]),
     "hrt_net_destroy": (C.c_int, [_vp]),
     "hrt_net_num_params": (C.c_int64, [_vp]),
     "hrt_net_get_params": (C.c_int, [_vp, _vp, _i64]),

@@ -15,7 +15,7 @@ from tests.gpu_helpers import spherical_test_grid, workload_from_walls
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT]
+KERNELS = [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT, hrt.HRT_KERNEL_REGROUP]
 
 
 def _walls(grid):

@@ -64,7 +64,7 @@ def _lockstep(m, st, om, ref, median_tol=1e-4):
     assert st["n_crossings"] == pytest.approx(ref["n_crossings"], rel=2e-3)
 
 
-@pytest.mark.parametrize("kernel", [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT])
+@pytest.mark.parametrize("kernel", [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT, hrt.HRT_KERNEL_REGROUP])
 def test_cylindrical_disk_iterations_match_oracle(kernel):
     wl = W.cylindrical_disk(n_R=60, n_z=48, n_packets=200_000)
     om = M.OracleModel(wl)

@@ -16,7 +16,7 @@ from paper_1112_1071_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT]
+KERNELS = [hrt.HRT_KERNEL_PLAIN, hrt.HRT_KERNEL_EVENT, hrt.HRT_KERNEL_REGROUP]
 
 
 def _disk():
