@@ -108,3 +108,18 @@ def as_device_sees(p, wl):
     p32 = np.asarray(p, np.float64).astype(np.float32)
     seen = p32 * np.float32(1.0 / L0)          # FP32 product, rounded like the device's
     return p32, seen.astype(np.float64) * L0
+
+
+def pixel_parity(img, ref, tol=1e-4):
+    """Per-pixel agreement of two images of the same packets (lockstep): over the pixels lit in
+    either, the fraction whose values differ by more than tol (relative to the larger), the median
+    relative difference, and the summed |difference| relative to the summed reference."""
+    import numpy as np
+    img = np.asarray(img, np.float64)
+    ref = np.asarray(ref, np.float64)
+    lit = (img > 0) | (ref > 0)
+    big = np.maximum(np.abs(img), np.abs(ref))[lit]
+    rel = np.abs(img - ref)[lit] / big
+    return {"lit": int(lit.sum()), "frac_off": float((rel > tol).mean()) if lit.any() else 0.0,
+            "median_rel": float(np.median(rel)) if lit.any() else 0.0,
+            "l1_rel": float(np.abs(img - ref).sum() / max(np.abs(ref).sum(), 1e-300))}

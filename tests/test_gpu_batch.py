@@ -48,6 +48,43 @@ def test_batched_models_match_individual_runs():
     L.hrt_batch_destroy(b)
 
 
+def test_batched_models_match_the_oracle_in_lockstep():
+    """A mixed batch (two uneven spherical-polar disks and the Cartesian tiny sphere) in one
+    persistent launch against the FP64 oracle on each model's own Philox streams: energy
+    conservation to FP64 rounding, and per-cell deposits and temperatures in lockstep over two
+    Lucy iterations (Sect. 2.3, Eq. 2-3; the second re-emits from the first's temperatures)."""
+    from oracle import mc as M
+    L = hrt.load()
+    wls = W.batched_disks(n_models=2, size_scale=0.15, packet_scale=0.005, seed=34)
+    wls.append(W.tiny_sphere(n_packets=20_000))
+    models = [hrt.Model(wl) for wl in wls]
+    oms = [M.OracleModel(wl) for wl in wls]
+    npk = np.array([wl.n_packets for wl in wls], np.int64)
+    b = _batch(models)
+    p = hrt.default_params(q_thres=1.0)
+    stats = (hrt.hrt_iter_stats * len(wls))()
+    iters = C.c_int()
+    for it in range(2):
+        assert L.hrt_batch_run(b, npk.ctypes.data, 1, C.byref(p), stats, C.byref(iters)) == 0
+        assert iters.value == 1
+        for m, (mb, om) in enumerate(zip(models, oms)):
+            ref = om.run_iteration(n_packets=int(npk[m]), nthreads=8)
+            sb = stats[m]
+            assert sb.iteration == it
+            assert sb.e_escaped + sb.e_killed == pytest.approx(om.L_tot, rel=1e-12)
+            assert sb.n_crossings == pytest.approx(ref["n_crossings"], rel=2e-3)
+            acc, racc = mb.absorbed(), ref["acc"]
+            seen = racc > 0
+            rel = np.abs(acc[seen] - racc[seen]) / racc[seen]
+            assert np.median(rel) < 1e-4, (m, it, np.median(rel))
+            assert abs(acc.sum() - racc.sum()) <= 2e-3 * racc.sum(), (m, it)
+            T, rT = mb.temperature(), ref["T"]
+            dust = om.rho > 0
+            dT = np.abs(T[dust] - rT[dust]) / rT[dust]
+            assert np.median(dT) < 1e-4 and dT.mean() < 0.01, (m, it, np.median(dT), dT.mean())
+    L.hrt_batch_destroy(b)
+
+
 def test_converged_models_drop_out():
     L = hrt.load()
     wls = W.batched_disks(n_models=5, size_scale=0.2, packet_scale=0.005, seed=32)

@@ -13,6 +13,7 @@ import pytest
 from oracle import mc as M
 from paper_1112_1071_gb300 import hrt
 from paper_1112_1071_gb300 import workloads as W
+from tests.gpu_helpers import pixel_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -83,4 +84,9 @@ def test_turbulent_cloud_full_size():
     m3, st3, ref3 = _share(wl, om, 33_000_000, 20_000, n_total, peel=1, update_temperature=0)
     img, ri = m3.image(), ref3["img"]
     np.testing.assert_allclose(img.sum(axis=(2, 3)), ri.sum(axis=(2, 3)), rtol=2e-2)
+    # pixel by pixel (the share's packets peel into the same 512^2 pixels on both sides)
+    stats = pixel_parity(img, ri)
+    print("cloud image pixels", stats)
+    assert stats["lit"] > 400
+    assert stats["median_rel"] < 1e-6 and stats["frac_off"] < 0.01 and stats["l1_rel"] < 1e-4
     np.testing.assert_allclose(m3.sed().sum(axis=1), ref3["sed"].sum(axis=1), rtol=1e-3)
