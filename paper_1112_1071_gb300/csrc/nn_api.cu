@@ -280,16 +280,15 @@ __global__ void k_from_temperature(const double* T, float* y, long long n) {
 
 extern "C" {
 
-int hrt_net_create(hrt_net** out, int device, int base_channels, int levels, uint64_t seed, void* stream) {
-    if (!out || base_channels < 32 || base_channels % 32 != 0 || levels < 1 || levels > 4) return HRT_EINVAL;
+static int net_create(hrt_net** out, int device, const int* widths, int levels, uint64_t seed, void* stream) {
     *out = nullptr;
     hrt_net* n = new hrt_net();
     n->device = device;
     n->stream = (cudaStream_t)stream;
-    n->base = base_channels;
+    n->base = widths[0];
     n->levels = levels;
     Guard gd(device);
-    for (int l = 0; l <= levels; ++l) n->ch.push_back(base_channels << l);
+    for (int l = 0; l <= levels; ++l) n->ch.push_back(widths[l]);
     long long off = 0;
     auto add = [&](int cin_real, int cin, int cout) {
         Layer ly;
@@ -350,6 +349,20 @@ int hrt_net_create(hrt_net** out, int device, int base_channels, int levels, uin
     }
     *out = n;
     return HRT_OK;
+}
+
+int hrt_net_create(hrt_net** out, int device, int base_channels, int levels, uint64_t seed, void* stream) {
+    if (!out || base_channels < 32 || base_channels % 32 != 0 || levels < 1 || levels > 4) return HRT_EINVAL;
+    int w[5];
+    for (int l = 0; l <= levels; ++l) w[l] = base_channels << l;
+    return net_create(out, device, w, levels, seed, stream);
+}
+
+int hrt_net_create_widths(hrt_net** out, int device, const int* widths, int levels, uint64_t seed, void* stream) {
+    if (!out || !widths || levels < 1 || levels > 4) return HRT_EINVAL;
+    for (int l = 0; l <= levels; ++l)
+        if (widths[l] < 32 || widths[l] % 32 != 0 || widths[l] > 512) return HRT_EINVAL;
+    return net_create(out, device, widths, levels, seed, stream);
 }
 
 int hrt_net_destroy(hrt_net* n) {
