@@ -377,10 +377,15 @@ int hrt_net_warm_start(hrt_net* net, hrt_ctx* ctx);
  * GPU never reaches): the block that gave up frees its tensor memory while its own MMAs may
  * still be running, so treat the outputs of that call, and of any later tensor-core call in the
  * process, as invalid; the network calls (hrt_net_*) return the same code and leave the weights
- * of a failed training step unchanged, and the caller should recompute or stop.  hrt_nn_conv3d_mma is the same forward convolution with
- * warp-level mma.sync, the baseline the tcgen05 kernel is measured against. */
+ * of a failed training step unchanged, and the caller should recompute or stop.
+ * hrt_nn_conv3d runs the TMA-fed pipelined kernel (persistent CTAs; operand stages loaded by TMA
+ * overlap the MMAs); hrt_nn_conv3d_phased the same convolution loading each phase's operands with
+ * cp.async before its MMAs; hrt_nn_conv3d_mma the same with warp-level mma.sync, the baseline the
+ * tcgen05 kernels are measured against. */
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
                   int relu, float* d_y, void* stream);
+int hrt_nn_conv3d_phased(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                         const float* d_b, int relu, float* d_y, void* stream);
 int hrt_nn_conv3d_mma(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
                       const float* d_b, int relu, float* d_y, void* stream);
 int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,

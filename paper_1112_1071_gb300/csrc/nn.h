@@ -16,6 +16,8 @@ using bf16 = __nv_bfloat16;
 // warp-level mma.sync, kept as the measured baseline.
 cudaError_t conv3d(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
                    int Cout, bool flip, bool relu, cudaStream_t s);
+cudaError_t conv3d_phased(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
+                   int Cout, bool flip, bool relu, cudaStream_t s);
 cudaError_t conv3d_mma(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W,
                        int Cin, int Cout, bool flip, bool relu, cudaStream_t s);
 // after a synchronisation of s: *failed = 1 if a tcgen05 convolution block gave up a wait

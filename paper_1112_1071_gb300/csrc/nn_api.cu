@@ -553,21 +553,28 @@ int hrt_net_warm_start(hrt_net* n, hrt_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------- single-layer hooks
+// which kernel a hook runs: the TMA-fed pipeline, the per-phase tcgen05 kernel, or mma.sync
+enum ConvImpl { CONV_TMA = 0, CONV_PHASED = 1, CONV_MMA = 2 };
 static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
-                       const float* d_b, int relu, float* d_y, void* stream, bool legacy);
+                       const float* d_b, int relu, float* d_y, void* stream, int impl);
 
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,
                   int relu, float* d_y, void* stream) {
-    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, false);
+    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, CONV_TMA);
+}
+
+int hrt_nn_conv3d_phased(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
+                         const float* d_b, int relu, float* d_y, void* stream) {
+    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, CONV_PHASED);
 }
 
 int hrt_nn_conv3d_mma(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
                       const float* d_b, int relu, float* d_y, void* stream) {
-    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, true);
+    return conv3d_hook(N, D, H, W, Cin, Cout, d_x, d_w, d_b, relu, d_y, stream, CONV_MMA);
 }
 
 static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w,
-                       const float* d_b, int relu, float* d_y, void* stream, bool legacy) {
+                       const float* d_b, int relu, float* d_y, void* stream, int impl) {
     if (N < 1 || D < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32 || !d_x || !d_w || !d_y) return HRT_EINVAL;
     const cudaStream_t s = (cudaStream_t)stream;
     const long long NV = (long long)N * D * H * W;
@@ -579,8 +586,9 @@ static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const floa
     if (e == cudaSuccess) e = nn::f32_to_bf16(d_x, x, NV * Cin, s);
     if (e == cudaSuccess) e = nn::weights_bf16(d_w, wb, wt, Cin, Cin, Cout, s);
     if (e == cudaSuccess)
-        e = legacy ? nn::conv3d_mma(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
-                   : nn::conv3d(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
+        e = impl == CONV_MMA      ? nn::conv3d_mma(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
+            : impl == CONV_PHASED ? nn::conv3d_phased(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
+                                  : nn::conv3d(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
     if (e == cudaSuccess) e = nn::bf16_to_f32(y, d_y, NV * Cout, s);
     int failed = 0;
     if (e == cudaSuccess) e = nn::tc_status(&failed, s);

@@ -16,6 +16,7 @@
 // resident blocks overlap their loads with these MMAs.  The epilogue reads each voxel's row of
 // the accumulator with tcgen05.ld, adds the bias, applies ReLU and stores BF16.  Every wait is
 // bounded (2 s): past it the block records an error, frees its tensor memory and returns.
+#include <cuda.h>          // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -222,12 +223,303 @@ static cudaError_t launch_tc(const bf16* in, const bf16* Bw, const float* bias, 
     return cudaGetLastError();
 }
 
-cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
-                   int Cout, bool flip, bool relu, cudaStream_t s) {
+cudaError_t conv3d_phased(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W,
+                          int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     if (Cin % 16 != 0 || Cout % 32 != 0 || Cin <= 0 || Cout <= 0) return cudaErrorInvalidValue;
     if (Cout % 128 == 0) return launch_tc<128>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
     if (Cout % 64 == 0) return launch_tc<64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
     return launch_tc<32>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+}
+
+// ---------------------------------------------------------------- TMA-fed, pipelined convolution
+// The same implicit GEMM as k_conv3d_tc, arranged for Blackwell's asynchronous units.  A
+// persistent CTA per SM walks its share of (image, z, 16 x 8 brick, output-channel tile) work
+// items with three roles: one thread loads, per 16-channel chunk, the halo (one box of 10 x 18 x
+// 3 voxels per 8-channel half) and all 27 taps' weights with TMA into one of the shared-memory
+// stages; one thread issues the chunk's 27 MMAs into one of two tensor-memory accumulators as
+// soon as the stage has landed and hands the stage back when they complete; four epilogue warps
+// drain the other accumulator (bias, ReLU, BF16 store) meanwhile.  The loads of the next chunks
+// thus overlap the MMAs of this one, and a tile's epilogue the next tile's MMAs.  A TMA box of 8
+// channels (16 bytes) x voxels along x puts each voxel's 8 channels in one 16-byte row, so 8
+// consecutive voxels of one (z, y) row are a no-swizzle K-major core matrix; the box holds 10
+// voxels along x, so the three x shifts of a tap are the same box read 0, 16 or 32 bytes further
+// into each 160-byte row (the stride byte offset of the operand descriptor), and the halo is
+// loaded once, not three times; the second channel half lies one region further (its leading
+// byte offset).  The weights land the same way, 8 output channels per core matrix.  Every wait
+// gives up after WAIT_LIMIT_NS (or when another role has given up): the block records the error,
+// lets its own loads and MMAs drain (bounded), frees its tensor memory and returns.
+constexpr int TM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
+constexpr int TM_HX = BRICK_X + 2;                  // halo voxels along x
+constexpr int TM_ROW = TM_HX * 16;                  // one (z, y) row of one channel half: 160 bytes
+constexpr int TM_HALF_BYTES = 3 * HALO_Y * TM_ROW;  // one channel half of the halo (what TMA delivers)
+constexpr int TM_HALF = (TM_HALF_BYTES + 127) & ~127;   // its region, 128-byte aligned
+
+template <int BN>
+struct TmShape {
+    static constexpr int WHALF = 27 * BN * 16;      // one channel half of all taps' weights
+    static constexpr int STAGE = 2 * TM_HALF + 2 * WHALF;
+    static constexpr int TX = 2 * TM_HALF_BYTES + 2 * WHALF;       // bytes a stage's loads deliver
+    static constexpr int STAGES = BN <= 32 ? 4 : 3;                // as many as fit in 227 KB
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 128;       // + alignment slack, barriers
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TM_THREADS, 1)
+    k_conv3d_tma(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap wts,
+                 const float* __restrict__ bias, bf16* __restrict__ out, int N, int D, int H, int W, int Cin, int Cout,
+                 int flip, int relu) {
+    constexpr int STAGE = TmShape<BN>::STAGE, WHALF = TmShape<BN>::WHALF, TM_STAGES = TmShape<BN>::STAGES;
+    constexpr uint32_t NCOLS = 2 * BN;
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, BN);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = tc::smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sbar = base + TM_STAGES * STAGE;
+    unsigned char* const gbar = smem_raw + (sbar - raw);
+    auto full = [&](int st) { return sbar + 8u * st; };
+    auto empty = [&](int st) { return sbar + 8u * (TM_STAGES + st); };
+    auto accf = [&](int b) { return sbar + 8u * (2 * TM_STAGES + b); };
+    auto acce = [&](int b) { return sbar + 8u * (2 * TM_STAGES + 2 + b); };
+    const uint32_t drain = sbar + 8u * (2 * TM_STAGES + 4);
+    const uint32_t slot = sbar + 8u * (2 * TM_STAGES + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 8 * (2 * TM_STAGES + 5) + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int st = 0; st < TM_STAGES; ++st) {
+            tc::mbar_init(full(st), 1);
+            tc::mbar_init(empty(st), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(accf(b), 1);
+            tc::mbar_init(acce(b), 128);
+        }
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, NCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot) : "memory");
+
+    // a bounded wait that also gives up once another role has (drains wait out their time)
+    auto wait = [&](uint32_t bar, uint32_t parity, bool drain_wait = false) -> bool {
+        const uint64_t t0 = tc::global_ns();
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity)
+                : "memory");
+            if (done) return true;
+            if ((*abort_flag && !drain_wait) || tc::global_ns() - t0 > WAIT_LIMIT_NS) {
+                *abort_flag = 1;
+                atomicExch(&g_tc_error, 1);
+                return false;
+            }
+        }
+    };
+
+    const int nbx = (W + BRICK_X - 1) / BRICK_X, nby = (H + BRICK_Y - 1) / BRICK_Y, ntn = Cout / BN;
+    const long long ntiles = (long long)N * D * nby * nbx * ntn;
+    const int kchunks = Cin / KC;
+    auto decode = [&](long long t, int& b, int& z, int& y0, int& x0, int& n0) {
+        n0 = (int)(t % ntn) * BN;
+        t /= ntn;
+        x0 = (int)(t % nbx) * BRICK_X;
+        t /= nbx;
+        y0 = (int)(t % nby) * BRICK_Y;
+        t /= nby;
+        z = (int)(t % D);
+        b = (int)(t / D);
+    };
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            tc::tma_prefetch_map(&act);
+            tc::tma_prefetch_map(&wts);
+            long long it = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int b, z, y0, x0, n0;
+                decode(t, b, z, y0, x0, n0);
+                for (int c = 0; c < kchunks && ok; ++c, ++it) {
+                    const int st = (int)(it % TM_STAGES);
+                    const uint32_t use = (uint32_t)(it / TM_STAGES);
+                    if (!wait(empty(st), (use & 1u) ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sb = base + st * STAGE;
+                    tc::mbar_arrive_expect_tx(full(st), (uint32_t)TmShape<BN>::TX);
+                    for (int h = 0; h < 2; ++h)
+                        tc::tma_load_5d(sb + h * TM_HALF, &act, c * KC + h * 8, x0 - 1, y0 - 1, z - 1, b, full(st));
+                    for (int h = 0; h < 2; ++h)
+                        tc::tma_load_3d(sb + 2 * TM_HALF + h * WHALF, &wts, c * KC + h * 8, n0, 0, full(st));
+                }
+            }
+            // no copy may still be landing when the block leaves: wait for the last stages issued
+            for (long long k = it - TM_STAGES; k < it; ++k)
+                if (k >= 0) wait(full((int)(k % TM_STAGES)), (uint32_t)((k / TM_STAGES) & 1), true);
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            long long it = 0;
+            int j = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+                const int buf = j & 1;
+                if (!wait(acce(buf), (((uint32_t)j >> 1) & 1u) ^ 1u)) break;
+                tc::fence_after_sync();
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                for (int c = 0; c < kchunks; ++c, ++it) {
+                    const int st = (int)(it % TM_STAGES);
+                    if (!wait(full(st), (uint32_t)((it / TM_STAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sb = base + st * STAGE;
+#pragma unroll 1
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                        const uint32_t a = sb + (dz * HALO_Y + dy) * TM_ROW + dx * 16;
+                        const uint32_t bw = sb + 2 * TM_HALF + (flip ? 26 - tap : tap) * BN * 16;
+                        tc::mma_bf16(acc, tc::smem_desc(a, TM_HALF, TM_ROW), tc::smem_desc(bw, WHALF, 128), IDESC,
+                                     (c > 0 || tap > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(empty(st));          // the stage is free once these MMAs complete
+                }
+                if (ok) tc::mma_commit(accf(buf));
+            }
+            // every MMA this thread issued has completed before tensor memory is freed
+            tc::mma_commit(drain);
+            wait(drain, 0u, true);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 0-3)
+        int j = 0;
+        const long long V = (long long)D * H * W;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int buf = j & 1;
+            bool got = true;
+            if (lane == 0) got = wait(accf(buf), ((uint32_t)j >> 1) & 1u);
+            if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) break;
+            tc::fence_after_sync();
+            int b, z, y0, x0, n0;
+            decode(t, b, z, y0, x0, n0);
+            const int yy = y0 + tid / BRICK_X, xx = x0 + tid % BRICK_X;
+            const bool vin = yy < H && xx < W;
+            bf16* outb = out + (long long)b * V * Cout;
+            const long long v = ((long long)z * H + yy) * W + xx;
+            const uint32_t row_addr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float accv[16];
+                tc::tmem_ld16(row_addr + (uint32_t)c0, accv);
+                if (vin) {
+                    __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int n = n0 + c0 + 2 * i;
+                        float a0 = accv[2 * i] + (bias ? bias[n] : 0.f);
+                        float a1 = accv[2 * i + 1] + (bias ? bias[n + 1] : 0.f);
+                        if (relu) {
+                            a0 = fmaxf(a0, 0.f);
+                            a1 = fmaxf(a1, 0.f);
+                        }
+                        o[i] = __floats2bfloat162_rn(a0, a1);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(outb + v * Cout + n0 + c0);
+                    dst[0] = *reinterpret_cast<const uint4*>(&o[0]);
+                    dst[1] = *reinterpret_cast<const uint4*>(&o[4]);
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(acce(buf));
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+namespace {
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+    static std::atomic<void*> fn{nullptr};
+    void* f = fn.load(std::memory_order_acquire);
+    if (!f) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        fn.store(f, std::memory_order_release);
+    }
+    return reinterpret_cast<EncodeTiled>(f);
+}
+}  // namespace
+
+template <int BN>
+static cudaError_t launch_tma(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W,
+                              int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap act, wts;
+    const cuuint64_t adim[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t astr[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
+                                (cuuint64_t)D * H * W * Cin * 2};
+    const cuuint32_t abox[5] = {8, TM_HX, HALO_Y, 3, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), adim, astr, abox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const cuuint64_t wdim[3] = {(cuuint64_t)Cin, (cuuint64_t)Cout, 27};
+    const cuuint64_t wstr[2] = {(cuuint64_t)Cin * 2, (cuuint64_t)Cout * Cin * 2};
+    const cuuint32_t wbox[3] = {8, BN, 27};
+    if (enc(&wts, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Bw), wdim, wstr, wbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    constexpr int SMEM = TmShape<BN>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long ntiles = (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + BRICK_X - 1) / BRICK_X) * (Cout / BN);
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    k_conv3d_tma<BN><<<grid, TM_THREADS, SMEM, s>>>(act, wts, bias, out, N, D, H, W, Cin, Cout, flip ? 1 : 0,
+                                                    relu ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// The TMA-fed kernel for output tiles of 64 channels (Cout % 64 == 0), the phased kernel for the
+// rest: measured on GB300 (ncu, kernel time), the pipeline is 1.2-1.4x faster at 64-channel tiles
+// (2 x 64^3, 64 -> 64: 0.278 against 0.381 ms) and no faster at 32 (4 x 64^3, 32 -> 32: 0.303
+// against 0.291 ms), where each chunk's 2,800 16-byte TMA rows, not the MMAs, set the pace.
+cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
+                   int Cout, bool flip, bool relu, cudaStream_t s) {
+    if (Cin % 16 != 0 || Cout % 32 != 0 || Cin <= 0 || Cout <= 0) return cudaErrorInvalidValue;
+    if (Cout % 64 == 0 && encode_tiled()) return launch_tma<64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    return conv3d_phased(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
 
 // ---------------------------------------------------------------- weight gradient

@@ -131,6 +131,7 @@ _SIGS = {
     "hrt_net_warm_start": (C.c_int, [_vp, _vp]),
     "hrt_nn_conv3d": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, C.c_int, _vp, _vp]),
     "hrt_nn_conv3d_mma": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "hrt_nn_conv3d_phased": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, C.c_int, _vp, _vp]),
     "hrt_nn_conv3d_backward": (C.c_int, [C.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hrt_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int]),
     "hrt_batch_destroy": (C.c_int, [_vp]),
