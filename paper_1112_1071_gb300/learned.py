@@ -14,7 +14,7 @@ included) until the 99th percentile of the iteration change in T is below 2 %, a
 percentile stops changing (Delta < 1.02).  The Monte-Carlo iteration decides the result; the two
 arms' final temperatures are compared against the Monte-Carlo noise of one iteration.
 
-    python -m paper_1112_1071_gb300.learned --n 128 --train 2000 --test 8
+    python -m paper_1112_1071_gb300.learned --n 128 --train 2000 --test 4 --q-packets 8000000000
 """
 from __future__ import annotations
 
@@ -29,14 +29,20 @@ from . import hrt
 from . import workloads as W
 
 
-def solve(m, packets, max_iter, q_thres=1.02):
-    """Lucy iterations; returns the per-iteration percentile Q (Eqs. 4-5) and device ms."""
-    qs, ms = [], []
+def solve(m, packets, max_iter, q_thres=1.02, torch=None):
+    """Lucy iterations; returns the per-iteration percentile Q (Eqs. 4-5), device ms and (with
+    torch) each iteration's temperatures on the device."""
+    L = hrt.load()
+    qs, ms, Ts = [], [], []
     for _ in range(max_iter):
         st = m.run_iteration(n_packets=packets, q_thres=q_thres)
         qs.append(st["Q"])
         ms.append(st["ms_total"])
-    return dict(q=qs, ms=ms)
+        if torch is not None:
+            T = torch.empty(m.ncells, dtype=torch.float64, device="cuda")
+            hrt.check(m.ctx, L.hrt_get_temperature_device(m.ctx, T.data_ptr(), T.numel()))
+            Ts.append(T)
+    return dict(q=qs, ms=ms, T=Ts)
 
 
 def field(m, torch):
@@ -67,8 +73,8 @@ def generate(seeds, n, packets, iters, tau, torch, log=None):
 
 
 def bench_conv(torch, log, reps=5):
-    """Device time per launch of the 'same' 3x3x3 convolution through its two C-ABI hooks
-    (tcgen05 with the accumulator in tensor memory, and the mma.sync baseline) on three shapes,
+    """Device time per launch of the 'same' 3x3x3 convolution through its three C-ABI hooks
+    (tcgen05 fed by TMA, tcgen05 with per-phase cp.async loads, and the mma.sync baseline) on three shapes,
     by CUDA events around reps calls each (the hooks' BF16 conversions included)."""
     L = hrt.load()
     out = []
@@ -78,7 +84,8 @@ def bench_conv(torch, log, reps=5):
         b = torch.zeros(cout, device="cuda")
         y = torch.empty((n, d, d, d, cout), device="cuda")
         row = dict(shape=f"{n}x{d}^3 {cin}->{cout}", gflop=2 * 27 * cin * cout * n * d ** 3 / 1e9)
-        for name, f in (("tcgen05", L.hrt_nn_conv3d), ("mma_sync", L.hrt_nn_conv3d_mma)):
+        for name, f in (("tcgen05_tma", L.hrt_nn_conv3d), ("tcgen05_phased", L.hrt_nn_conv3d_phased),
+                        ("mma_sync", L.hrt_nn_conv3d_mma)):
             for _ in range(2):
                 hrt.check(None, f(n, d, d, d, cin, cout, x.data_ptr(), w.data_ptr(), b.data_ptr(), 1, y.data_ptr(), None))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -143,13 +150,13 @@ def evaluate(net, seeds, n, packets, max_iter, tau, torch, log=None):
         wl = W.warmstart_cloud(int(s), n=n, n_packets=packets, n_iter=max_iter, tau_mean_550=tau)
         cold = hrt.Model(wl)
         Tprev = torch.empty(cold.ncells, dtype=torch.float64, device="cuda")
-        rc_ = solve(cold, packets, max_iter)
+        rc_ = solve(cold, packets, max_iter, torch=torch)
         warm = hrt.Model(wl)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hrt.check(warm.ctx, L.hrt_net_warm_start(net, warm.ctx))
         infer_ms = 1e3 * (time.perf_counter() - t0)
-        rw_ = solve(warm, packets, max_iter)
+        rw_ = solve(warm, packets, max_iter, torch=torch)
         Tc = torch.empty_like(Tprev)
         Tw = torch.empty_like(Tprev)
         hrt.check(cold.ctx, L.hrt_get_temperature_device(cold.ctx, Tc.data_ptr(), Tc.numel()))
@@ -161,8 +168,13 @@ def evaluate(net, seeds, n, packets, max_iter, tau, torch, log=None):
         cold.run_iteration(n_packets=packets)
         hrt.check(cold.ctx, L.hrt_get_temperature_device(cold.ctx, Tc.data_ptr(), Tc.numel()))
         noise = float(((Tc - Tprev).abs() / Tprev)[dust].mean())
+        # distance of every iteration's field to the converged one (the cold arm's last), mean |dT|/T
+        dist = {arm: [float(((T - Tprev).abs() / Tprev)[dust].mean()) for T in r["T"]] for arm, r in
+                (("cold", rc_), ("warm", rw_))}
+        for r in (rc_, rw_):
+            r.pop("T")
         row = dict(seed=int(s), sources=len(wl.sources), inference_ms=infer_ms, cold=rc_, warm=rw_,
-                   final_mean_dT_warm_vs_cold=agree, mc_noise_mean_dT=noise)
+                   final_mean_dT_warm_vs_cold=agree, mc_noise_mean_dT=noise, dist_to_converged=dist)
         for name, r, extra in (("cold", rc_, 0.0), ("warm", rw_, infer_ms)):
             for crit, it in (("q", converged_at(r["q"], 1.02)), ("delta", converged_at(r["q"], 2.0, 1.02))):
                 row[f"{name}_iters_to_{crit}"] = it
@@ -178,6 +190,80 @@ def evaluate(net, seeds, n, packets, max_iter, tau, torch, log=None):
     return rows
 
 
+def batch_solve(models, packets, max_iter, q_thres, delta_thres):
+    """Lucy iterations of several models in one persistent launch per iteration (hrt_batch_run),
+    each dropping out once its own convergence test passes; returns (wall ms of the run, per-model
+    number of the iteration at which it converged or None)."""
+    import torch
+    L = hrt.load()
+    arr = (C.c_void_p * len(models))(*[m.ctx.value for m in models])
+    b = C.c_void_p()
+    hrt.check(None, L.hrt_batch_create(C.byref(b), arr, len(models)))
+    npk = np.full(len(models), packets, np.int64)
+    p = hrt.default_params(q_thres=q_thres, delta_thres=delta_thres)
+    stats = (hrt.hrt_iter_stats * len(models))()
+    iters = C.c_int()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hrt.check(None, L.hrt_batch_run(b, npk.ctypes.data, max_iter, C.byref(p), stats, C.byref(iters)))
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
+    L.hrt_batch_destroy(b)
+    return ms, [stats[m].iteration + 1 if stats[m].converged else None for m in range(len(models))]
+
+
+def evaluate_batch(net, seeds, n, packets, max_iter, tau, q_thres, delta_thres, torch, log=None):
+    """Time to convergence of several held-out clouds (Sect. 2.4, Eqs. 4-6, with q_thres and
+    delta_thres): the plain GPU iteration (cold start from 10 K, one model after the other),
+    the cold start batched (one persistent launch per iteration for all clouds, converged clouds
+    dropping out), and the warm start batched (the network's prediction for every cloud first,
+    its inference time included).  Every arm runs the same packets on the same random streams."""
+    L = hrt.load()
+    wls = [W.warmstart_cloud(int(s), n=n, n_packets=packets, n_iter=max_iter, tau_mean_550=tau) for s in seeds]
+    p = hrt.default_params(q_thres=q_thres, delta_thres=delta_thres)
+    # plain: one model at a time, each until its own test passes
+    plain_ms, plain_it = 0.0, []
+    for wl in wls:
+        m = hrt.Model(wl)
+        it = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(max_iter):
+            st = m.run_iteration(n_packets=packets, params=p)
+            if st["converged"]:
+                it = i + 1
+                break
+        torch.cuda.synchronize()
+        plain_ms += 1e3 * (time.perf_counter() - t0)
+        plain_it.append(it)
+        m.close()
+    cold = [hrt.Model(wl) for wl in wls]
+    cold_ms, cold_it = batch_solve(cold, packets, max_iter, q_thres, delta_thres)
+    warm = [hrt.Model(wl) for wl in wls]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in warm:
+        hrt.check(m.ctx, L.hrt_net_warm_start(net, m.ctx))
+    torch.cuda.synchronize()
+    infer_ms = 1e3 * (time.perf_counter() - t0)
+    warm_ms, warm_it = batch_solve(warm, packets, max_iter, q_thres, delta_thres)
+    dT = []
+    for mc, mw, wl in zip(cold, warm, wls):
+        Tc, Tw = mc.temperature(), mw.temperature()
+        dust = wl.rho.reshape(-1) > 0
+        dT.append(float(np.mean(np.abs(Tw[dust] - Tc[dust]) / Tc[dust])))
+        mc.close()
+        mw.close()
+    row = dict(clouds=len(wls), packets=packets, q_thres=q_thres, delta_thres=delta_thres,
+               plain_one_by_one_ms=plain_ms, plain_iterations=plain_it, cold_batched_ms=cold_ms,
+               cold_iterations=cold_it, warm_batched_ms=warm_ms + infer_ms, warm_inference_ms=infer_ms,
+               warm_iterations=warm_it, final_mean_dT_warm_vs_cold=dT,
+               speedup_vs_plain=plain_ms / (warm_ms + infer_ms), speedup_vs_cold_batched=cold_ms / (warm_ms + infer_ms))
+    if log:
+        log(json.dumps(row))
+    return row
+
+
 def _mean(xs):
     xs = [x for x in xs if x is not None]
     return float(np.mean(xs)) if xs else None
@@ -186,15 +272,20 @@ def _mean(xs):
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--tau", type=float, default=10.0, help="mean 550 nm optical depth across the cloud")
-    ap.add_argument("--train", type=int, default=256)
-    ap.add_argument("--test", type=int, default=16)
-    ap.add_argument("--packets", type=int, default=8_000_000, help="packets per iteration of a training field")
-    ap.add_argument("--iters", type=int, default=8, help="iterations of a training field")
-    ap.add_argument("--eval-packets", type=int, default=100_000_000)
-    ap.add_argument("--eval-iters", type=int, default=8)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=4)
+    ap.add_argument("--q-test", type=int, default=2, help="held-out clouds judged by Q_99(dT) < 1.02")
+    ap.add_argument("--packets", type=int, default=30_000_000, help="packets per iteration of a training field")
+    ap.add_argument("--iters", type=int, default=4, help="iterations of a training field")
+    ap.add_argument("--eval-packets", type=int, default=1_000_000_000,
+                    help="packets per iteration of the held-out runs judged by the Delta test")
+    ap.add_argument("--q-packets", type=int, default=0,
+                    help="packets per iteration of held-out runs judged by Q_99(dT) < 1.02 (0: skip); the "
+                         "Monte-Carlo noise floor of Q_99 must lie below 1.02 there")
+    ap.add_argument("--eval-iters", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--widths", default="32,64,192",
@@ -203,6 +294,8 @@ def main():
     ap.add_argument("--bench-conv", action="store_true",
                     help="only time the 3x3x3 convolution (tcgen05 and mma.sync hooks) on three shapes")
     a = ap.parse_args()
+    if not 0 <= a.q_packets < 2 ** 32 or not 0 < a.eval_packets < 2 ** 32:
+        ap.error("packets per iteration must be below 2^32 (the packet id is one 32-bit word of the Philox counter)")
     log = lambda s: print(s, flush=True)
     L = hrt.load()
     if a.bench_conv:
@@ -218,14 +311,20 @@ def main():
     t1 = time.time()
     hist = train(net, X, Y, a.epochs, a.lr, a.batch, torch, log)
     train_s = time.time() - t1
-    rows = evaluate(net, range(5000, 5000 + a.test), a.n, a.eval_packets, a.eval_iters, a.tau, torch, log)
+    held = range(5000, 5000 + a.test)
+    rows = evaluate(net, held, a.n, a.eval_packets, a.eval_iters, a.tau, torch, log)
+    batched = [evaluate_batch(net, held, a.n, a.eval_packets, a.eval_iters, a.tau, 2.0, 1.02, torch, log)]
+    if a.q_packets > 0:
+        batched.append(evaluate_batch(net, held[:a.q_test], a.n, a.q_packets, a.eval_iters, a.tau, 1.02, float("inf"),
+                                      torch, log))
     summary = dict(
         grid=a.n, tau_mean_550=a.tau, train_fields=a.train, test_fields=a.test, packets=a.packets,
         iters=a.iters, eval_packets=a.eval_packets, widths=widths, params=int(L.hrt_net_num_params(net)),
         generation_s=gen_s, training_s=train_s, epochs=a.epochs, final_loss=hist[-1],
         inference_ms_mean=_mean([r["inference_ms"] for r in rows]),
         final_mean_dT_warm_vs_cold=_mean([r["final_mean_dT_warm_vs_cold"] for r in rows]),
-        mc_noise_mean_dT=_mean([r["mc_noise_mean_dT"] for r in rows]), loss_history=hist, rows=rows, fields=info)
+        mc_noise_mean_dT=_mean([r["mc_noise_mean_dT"] for r in rows]), batched=batched, loss_history=hist, rows=rows,
+        fields=info)
     for arm in ("cold", "warm"):
         for crit in ("q", "delta"):
             summary[f"{arm}_iters_to_{crit}_mean"] = _mean([r[f"{arm}_iters_to_{crit}"] for r in rows])
