@@ -83,6 +83,15 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-kernel arm and the disk line")
     ap.add_argument("--rows", action="store_true",
                     help="measure the extension rows (MRW, raytracing, cylindrical grids, external field) instead")
+    ap.add_argument("--learned", action="store_true",
+                    help="time to converged temperatures of held-out 128^3 clouds: the learned warm start plus "
+                         "batching against the plain GPU iteration (one JSON line, not the headline)")
+    ap.add_argument("--learned-fields", type=int, default=256, help="training fields generated for --learned")
+    ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--batch", action="store_true",
+                    help="the 512 uneven disks of the batched workload at full packet budgets: one persistent "
+                         "launch per iteration against the same models one after the other (one JSON line)")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="packet-budget scale for --batch")
     ap.add_argument("--pda-min", type=int, default=6000,
                     help="disk line: packet entries below which a cell takes the diffusion approximation in "
                          "the time-to-converged solve with PDA (App. A); 0 skips that solve")
@@ -497,6 +506,10 @@ def main():
         return reference_arm(args, rank, world)
     if args.rows:
         return rows_bench(local)
+    if args.learned:
+        return learned_bench(args, local)
+    if args.batch:
+        return batch_bench(args, local)
 
     import torch
     from paper_1112_1071_gb300 import hrt
@@ -572,6 +585,99 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def learned_bench(args, local):
+    """Learned warm start (task pattern 4) on the configs of the warm-start workload: 128^3 clouds
+    with 1-8 stars (mean tau_550 = 10), a U-Net of widths 32, 64, 192 (2.19M parameters) trained by
+    the library's tensor-core kernels on fields that the plain GPU iteration produced, then four
+    held-out clouds solved to the Delta test (Q_99 < 2, Delta < 1.02; Eqs. 5-6) three ways with
+    1e9 packets per iteration on the same random streams: the plain GPU iteration from 10 K one
+    cloud after the other, the cold start batched in one persistent launch per iteration, and the
+    warm start batched (inference included)."""
+    import ctypes as C
+    import torch
+    from paper_1112_1071_gb300 import hrt, learned
+    torch.cuda.set_device(local)
+    L = hrt.load()
+    t0 = time.time()
+    X, Y, _ = learned.generate(range(1000, 1000 + args.learned_fields), 128, 30_000_000, 4, 10.0, torch)
+    gen_s = time.time() - t0
+    widths = (C.c_int * 3)(32, 64, 192)
+    net = C.c_void_p()
+    hrt.check(None, L.hrt_net_create_widths(C.byref(net), local, C.cast(widths, C.c_void_p), 2, 7, None))
+    t1 = time.time()
+    hist = learned.train(net, X, Y, args.learned_epochs, 1e-3, 4, torch)
+    train_s = time.time() - t1
+    del X, Y
+    row = learned.evaluate_batch(net, range(5000, 5004), 128, 1_000_000_000, 8, 10.0, 2.0, 1.02, torch)
+    line = {"metric": "time to converged temperatures, 4 held-out 128^3 clouds (warm start + batching)",
+            "value": row["warm_batched_ms"], "unit": "ms", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": row["warm_batched_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (network bf16 x bf16 -> f32)", "data": "synthetic",
+            "config": {"workload": "warmstart_cloud 128^3, 1-8 stars, mean tau_550=10; 1e9 packets per iteration; "
+                                   "criterion Q_99(dT) < 2 and Delta < 1.02", "training_fields": args.learned_fields,
+                       "epochs": args.learned_epochs, "params": int(L.hrt_net_num_params(net))},
+            "warm_vs_cold": row, "generation_s": gen_s, "training_s": train_s, "final_loss": hist[-1]}
+    print(json.dumps(line), flush=True)
+    L.hrt_net_destroy(net)
+    return 0
+
+
+def batch_bench(args, local):
+    """Batched models (task pattern 2): the 512 disks of the batched workload (tau_550 1-1e4, uneven
+    grids nr 50-400 x ntheta 32-200 x nphi 1-64, packet budgets log-uniform 1e5-1e7 per iteration)
+    advance `iters` Lucy iterations in one persistent launch per iteration (captured CUDA graph),
+    against the same models run one after the other (each iteration a launch of its own)."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    from paper_1112_1071_gb300 import hrt
+    from paper_1112_1071_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    L = hrt.load()
+    iters = 2
+    wls = W.batched_disks(n_models=512, packet_scale=args.batch_scale)
+    npk = np.array([wl.n_packets for wl in wls], np.int64)
+    never = hrt.default_params(q_thres=1.0)        # never converged: every model runs every iteration
+    # one by one
+    ms_one = 0.0
+    for wl in wls:
+        m = hrt.Model(wl, device=local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            m.run_iteration(params=never)
+        torch.cuda.synchronize()
+        ms_one += 1e3 * (time.perf_counter() - t0)
+        m.close()
+    # batched
+    models = [hrt.Model(wl, device=local) for wl in wls]
+    arr = (C.c_void_p * len(models))(*[m.ctx.value for m in models])
+    b = C.c_void_p()
+    hrt.check(None, L.hrt_batch_create(C.byref(b), arr, len(models)))
+    iters_run = C.c_int()
+    hrt.check(None, L.hrt_batch_run(b, npk.ctypes.data, 1, C.byref(never), None, C.byref(iters_run)))   # capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hrt.check(None, L.hrt_batch_run(b, npk.ctypes.data, iters, C.byref(never), None, C.byref(iters_run)))
+    torch.cuda.synchronize()
+    ms_batch = 1e3 * (time.perf_counter() - t0)
+    L.hrt_batch_destroy(b)
+    for m in models:
+        m.close()
+    total = int(npk.sum()) * iters
+    cells = int(sum(wl.rho.size for wl in wls))
+    line = {"metric": "photon packets/sec, 512 batched disk models (one persistent launch per iteration)",
+            "value": total / (ms_batch * 1e-3), "unit": "packets/s", "n_gpus": 1, "steps": iters, "warmup": 1,
+            "ms_per_step": ms_batch / iters, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched_disks 512 models, {cells} cells, {int(npk.sum())} packets per iteration "
+                                   f"(budgets log-uniform 1e5-1e7 x {args.batch_scale:g})", "iterations": iters},
+            "one_by_one": {"value": total / (ms_one * 1e-3), "ms_per_step": ms_one / iters},
+            "batched_over_one_by_one": ms_one / ms_batch}
+    print(json.dumps(line), flush=True)
     return 0
 
 
