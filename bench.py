@@ -65,7 +65,7 @@ B_REEMIT = 400.0
 # an ncu capture of the current k_event (a 1e6-packet Lucy launch on the full grid; DRAM traffic
 # there comes from the cache misses of the walk, so it grows with the crossings): per launch =
 # this x the launch's crossings
-TRAFFIC_PER_CROSSING = None
+TRAFFIC_PER_CROSSING = 51.9
 
 
 def parse():
