@@ -465,14 +465,16 @@ __global__ void __launch_bounds__(256, MINB) k_event_batch(const BatchModel* __r
     }
 }
 
+// deposit aggregation as for one model: on Cartesian grids only
 template <int G, int MINB>
 static void launch_batch_shape(const BatchModel* models, const BatchChunk* chunks, int nchunks, unsigned* chunk_counter,
                                const BatchState* state, int want_per_sm, int regroup, int sms, cudaStream_t s) {
+    constexpr bool WAGG = G == GRID_CARTESIAN;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<G, true, MINB>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event_batch<G, WAGG, MINB>, 256, 0);
     if (want_per_sm > 0 && want_per_sm < per_sm) per_sm = want_per_sm;
-    k_event_batch<G, true, MINB><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks, chunk_counter,
-                                                                                state, regroup);
+    k_event_batch<G, WAGG, MINB><<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(models, chunks, nchunks, chunk_counter,
+                                                                                 state, regroup);
 }
 
 // Default shape as for one model: 3 blocks of 256 per SM, regroup 20; the autotuner times others.
