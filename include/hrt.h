@@ -378,8 +378,9 @@ int hrt_net_warm_start(hrt_net* net, hrt_ctx* ctx);
  * still be running, so treat the outputs of that call, and of any later tensor-core call in the
  * process, as invalid; the network calls (hrt_net_*) return the same code and leave the weights
  * of a failed training step unchanged, and the caller should recompute or stop.
- * hrt_nn_conv3d runs the TMA-fed pipelined kernel (persistent CTAs; operand stages loaded by TMA
- * overlap the MMAs); hrt_nn_conv3d_phased the same convolution loading each phase's operands with
+ * hrt_nn_conv3d runs the TMA-fed pipelined kernel (persistent CTAs; operand stages -- the halo by
+ * TMA, the weights, packed per output-channel tile, by bulk copies -- overlap the MMAs);
+ * hrt_nn_conv3d_phased the same convolution loading each phase's operands with
  * cp.async before its MMAs; hrt_nn_conv3d_mma the same with warp-level mma.sync, the baseline the
  * tcgen05 kernels are measured against. */
 int hrt_nn_conv3d(int N, int D, int H, int W, int Cin, int Cout, const float* d_x, const float* d_w, const float* d_b,

@@ -342,7 +342,7 @@ int hrt_batch_tune(hrt_batch* b, const int64_t* n_packets) {
     int rc = build_batch(b, trial.data(), P);
     if (rc != HRT_OK) return done(rc);
     const int regroups[] = {12, 16, 20, 24};
-    const int per_sm[] = {2, 3};
+    const int per_sm[] = {2, 3, 4};
     float best = 1e30f;
     Launch best_l = b->launch;
     for (int bp : per_sm) {

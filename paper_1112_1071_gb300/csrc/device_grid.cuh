@@ -748,7 +748,9 @@ __device__ __forceinline__ void nudge(Ray& r) {
     r.p.z += h * r.u.z;
 }
 
-// Extinction optical depth from the ray's position to the grid edge (no deposit).
+// Extinction optical depth from the ray's position to the grid edge (no deposit), each crossing
+// counted in ncross; the walk stops once the depth passes tau_stop.  A ray that has not reached
+// the edge after MAX_WALK_STEPS crossings is dropped: F_INF.
 template <int G>
 __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi, unsigned long long& ncross,
                                              float tau_stop) {
@@ -766,7 +768,7 @@ __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi,
             else if (++zero_run > ZERO_RUN_LIMIT) { nudge(r); zero_run = 0; }
         }
     }
-    return tau;
+    return F_INF;
 }
 
 }  // namespace hrt

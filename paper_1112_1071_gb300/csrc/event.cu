@@ -2,14 +2,15 @@
 //
 // Every lane of a persistent warp runs a small state machine: it takes a packet, emits it,
 // walks it to its next event (interaction or escape), handles the event (scatter, or absorb
-// and re-emit), walks its peel-off rays, and takes the next packet when the history ends.
+// and re-emit), and takes the next packet when the history ends.
 // A round has two phases:
 //   * event phase: lanes with a finished walk handle their event (short, divergent code);
-//   * walk phase: all walking lanes (packet rays and peel rays share one step) take cell
-//     crossings together while at least `regroup` lanes are walking, so the walk -- where
-//     nearly all time goes -- runs in long converged loops.
-// In an imaging pass the peel rays that need a walk are queued instead (one record per event)
-// and walked afterwards by a separate pass, one ray per thread (peel.cu).
+//   * walk phase: all walking lanes take cell crossings together while at least `regroup`
+//     lanes are walking, so the walk -- where nearly all time goes -- runs in long converged
+//     loops.
+// In an imaging pass each event's peel-off rays are queued (one record per event) and walked
+// afterwards by a separate pass, one ray per thread (peel.cu); only events past the queue's
+// capacity are peeled by the lane itself, so the walk loop is the Lucy iterations' own.
 // Lanes that need a packet draw consecutive packet ids with one atomic per warp.  Packet p
 // always draws from its own Philox stream, so the histories do not depend on which lane or
 // launch shape runs them.  Deposits are the FP32 products kappa * l (scaled length), merged
@@ -24,7 +25,7 @@
 
 namespace hrt {
 
-enum LaneMode : int32_t { M_NEED = 0, M_WALK, M_PEEL, M_INTERACT, M_ESCAPED, M_PEEL_DONE, M_KILLED, M_DONE, M_MRW };
+enum LaneMode : int32_t { M_NEED = 0, M_WALK = 1, M_INTERACT = 3, M_ESCAPED = 4, M_KILLED = 6, M_DONE = 7, M_MRW = 8 };
 
 
 // The persistent lane state machine.  `fetch(need, lt_mask)` is called by the whole warp when
@@ -37,17 +38,15 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    Packet pk;                 // the packet; pk.r is the ray currently walked (packet or peel ray)
-    Ray saved;                 // packet ray while its peel rays are walked
+    Packet pk;                 // the packet
     float3 porg = make_float3(0.f, 0.f, 0.f);   // origin of the peel rays (event position)
     float3 uin = make_float3(0.f, 0.f, 1.f);    // incoming direction at a scattering (HG peel)
-    float tau = 0.f;           // optical depth left (packet) or accumulated (peel ray)
+    float tau = 0.f;           // optical depth left to the next interaction
     int32_t mode = M_NEED;
-    int32_t pobs = 0, pkind = PEEL_ISO, prelocate = 0;
     int32_t dep_ci = -1;
     float dep_val = 0.f;       // kappa * l (scaled length) merged while the packet stays in one cell
     int zero_run = 0;
-    unsigned ray_steps = 0;    // crossings of the current ray since it started or last interacted
+    unsigned ray_steps = 0;    // crossings of the packet since it started or last interacted
     bool aborted = false;
     // the walk's look-ahead: the density of the current cell, loaded one crossing ahead (when the
     // ray entered the cell), and (Cartesian) the next wall of every axis; `fresh` marks a ray that
@@ -69,49 +68,31 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         fresh = true;
         mode = M_WALK;
     };
-    // start peel ray `ob` from porg (cell of `saved`, or located along the observer direction);
-    // emission from a point source with precomputed columns needs no walk
-    auto start_peel = [&](int ob) {
-        if (prelocate && s.col) {
-            tau = pk.dust.chi * fmaxf(__ldg(s.col + (int64_t)pk.src * o.nobs + ob), 0.f);
-            mode = M_PEEL_DONE;
-            return;
-        }
-        pk.r = saved;
-        pk.r.p = porg;
-        set_dir(pk.r, make_float3(__ldg(o.n + 3 * ob), __ldg(o.n + 3 * ob + 1), __ldg(o.n + 3 * ob + 2)));
-        tau = 0.f;
-        ray_steps = 0;
-        zero_run = 0;
-        fresh = true;
-        mode = M_PEEL;
-        if (prelocate && !grid_locate<G>(g, pk.r)) mode = M_PEEL_DONE;
-    };
-    // after an emission or interaction: peel (if wanted) then draw a new optical depth
-    // raytraced: point-source emission or re-emission, which an a.rt pass raytraces instead
+    // after an emission or interaction: peel off (if wanted), then draw a new optical depth.
+    // raytraced: point-source emission or re-emission, which an a.rt pass raytraces instead.
+    // Peel rays that need a walk go to the queue of the peel pass while it has room; emission
+    // from a point source with precomputed columns, and events past the queue's capacity, are
+    // peeled here, one ray per observer (the lane's packet waits meanwhile; no random number is
+    // drawn, so the histories do not depend on which path peels)
     auto after_event = [&](int kind, int relocate, bool raytraced) {
         if constexpr (PEEL) {
             if (a.peel && pk.sbin >= 0 && o.nobs > 0 && !(raytraced && a.rt)) {
-                // peel rays that need a walk go to the queue of the peel pass while it has room
-                if (a.peel_q && !(relocate && s.col)) {
-                    const unsigned long long slot = atomicAdd(a.peel_n, 1ull);
-                    if (slot < (unsigned long long)a.peel_cap) {
-                        PeelEvent e;
-                        e.px = porg.x; e.py = porg.y; e.pz = porg.z;
-                        e.ci = relocate ? -1 : pk.r.ci;
-                        e.ux = uin.x; e.uy = uin.y; e.uz = uin.z;
-                        e.nu = kind == PEEL_HG ? -pk.nu : pk.nu;
-                        a.peel_q[slot] = e;
-                        start_walk();
-                        return;
-                    }
+                const bool cols = relocate && s.col;
+                unsigned long long slot = ~0ull;
+                if (a.peel_q && !cols) slot = atomicAdd(a.peel_n, 1ull);
+                if (slot < (unsigned long long)a.peel_cap) {
+                    PeelEvent e;
+                    e.px = porg.x; e.py = porg.y; e.pz = porg.z;
+                    e.ci = relocate ? -1 : pk.r.ci;
+                    e.ux = uin.x; e.uy = uin.y; e.uz = uin.z;
+                    e.nu = kind == PEEL_HG ? -pk.nu : pk.nu;
+                    a.peel_q[slot] = e;
+                } else {
+                    Ray at = pk.r;
+                    at.p = porg;
+                    peel_event<G>(g, d, o, a, t, st.sed, at, uin, kind, relocate != 0, pk.dust.chi, pk.sbin, lc,
+                                  cols ? s.col + (int64_t)pk.src * o.nobs : nullptr, PEEL_TAU_STOP);
                 }
-                saved = pk.r;
-                pkind = kind;
-                prelocate = relocate;
-                pobs = 0;
-                start_peel(0);
-                return;
             }
         }
         start_walk();
@@ -125,7 +106,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         if (!__shfl_sync(FULL, ab ? 1 : 0, 0)) return;
         aborted = true;
         if (mode == M_DONE) return;
-        lc.v[C_WATCHDOG]++;
+        lc.inc(C_WATCHDOG);
         const unsigned slot = atomicAdd(t.report_count, 1u);
         if (slot < (unsigned)WD_REPORTS) {
             float* r = t.report + slot * WD_FIELDS;
@@ -133,7 +114,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             r[4] = pk.r.p.x; r[5] = pk.r.p.y; r[6] = pk.r.p.z;
             r[7] = pk.r.u.x; r[8] = pk.r.u.y; r[9] = pk.r.u.z;
             r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
-            r[13] = pk.nu; r[14] = (float)pobs; r[15] = (float)where;
+            r[13] = pk.nu; r[14] = 0.f; r[15] = (float)where;
         }
         flush_run(t, dep_ci, dep_val);
         dep_ci = -1;
@@ -143,38 +124,8 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         flush_run(t, dep_ci, dep_val);
         dep_ci = -1;
         dep_val = 0.f;
-        lc.v[C_PACKETS_DONE]++;
+        lc.inc(C_PACKETS_DONE);
         mode = M_NEED;
-    };
-
-    // A peel ray has ended (edge, tau stop, precomputed column or start outside): tally its weight
-    // eps p exp(-tau) into the SED (and image) bins and start the next observer's ray, or give the
-    // lane back to its packet.  Called from the event phase and, so that a lane walking its peel
-    // rays never waits for the warp's next event phase, from the walk step itself.
-    auto finish_peels = [&]() {
-        do {
-            const float3 n = make_float3(__ldg(o.n + 3 * pobs), __ldg(o.n + 3 * pobs + 1), __ldg(o.n + 3 * pobs + 2));
-            const float prob = (pkind == PEEL_HG) ? hg_phase(d.g, dot3(uin, n)) : (0.25f / CUDART_PI_F);
-            const double w = a.eps * (double)(prob * expf(-tau));
-            if (st.sed) atomicAdd(st.sed + pobs * o.nsed + pk.sbin, w);
-            else atomicAdd(t.sed + (int64_t)pobs * o.nsed + pk.sbin, w);
-            if (o.nimg > 0) {
-                const float px = porg.x * __ldg(o.ex + 3 * pobs) + porg.y * __ldg(o.ex + 3 * pobs + 1) + porg.z * __ldg(o.ex + 3 * pobs + 2);
-                const float py = porg.x * __ldg(o.ey + 3 * pobs) + porg.y * __ldg(o.ey + 3 * pobs + 1) + porg.z * __ldg(o.ey + 3 * pobs + 2);
-                const int ix = (int)floorf((px + o.img_half) * o.img_scale);
-                const int iy = (int)floorf((py + o.img_half) * o.img_scale);
-                if (ix >= 0 && ix < o.img_nx && iy >= 0 && iy < o.img_ny)
-                    for (int l = 0; l < o.nimg; ++l)
-                        if (__ldg(o.img_bin + l) == pk.sbin)
-                            atomicAdd(t.img + (((int64_t)pobs * o.nimg + l) * o.img_ny + iy) * o.img_nx + ix, w);
-            }
-            if (++pobs < o.nobs) {
-                start_peel(pobs);
-            } else {
-                pk.r = saved;
-                start_walk();
-            }
-        } while (mode == M_PEEL_DONE);
     };
 
     // modified random walk (Sect. 2.2) at the start of a flight: one step per event phase while the
@@ -192,11 +143,11 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             return;
         }
         if (++pk.nint > a.max_interactions) {
-            lc.v[C_KILLED]++;
+            lc.inc(C_KILLED);
             end_packet();
             return;
         }
-        lc.v[C_MRW]++;
+        lc.inc(C_MRW);
         const float v = mrw_take(d, o, a, pk, R0);
         if (pk.r.ci == dep_ci) {
             dep_val += v;
@@ -216,20 +167,20 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         if (mode == M_KILLED) {
             end_packet();
         } else if (mode == M_ESCAPED) {
-            lc.v[C_ESCAPED]++;
+            lc.inc(C_ESCAPED);
             tally_escape(o, t, pk, st.esc);
             end_packet();
         } else if (mode == M_INTERACT) {
             if (++pk.nint > a.max_interactions) {
-                lc.v[C_KILLED]++;
+                lc.inc(C_KILLED);
                 end_packet();
             } else {
-                lc.v[C_INTERACTIONS]++;
+                lc.inc(C_INTERACTIONS);
                 const float z = pk.rng.next();
                 if (z > pk.dust.albedo) {
-                    lc.v[C_ABSORB]++;
+                    lc.inc(C_ABSORB);
                     if (a.terminate_on_absorb) {
-                        lc.v[C_ABSORBED_TERM]++;
+                        lc.inc(C_ABSORBED_TERM);
                         end_packet();
                     } else {
                         const float u1 = pk.rng.next(), u2 = pk.rng.next();
@@ -240,7 +191,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                         after_event(PEEL_ISO, 0, true);
                     }
                 } else {
-                    lc.v[C_SCATTER]++;
+                    lc.inc(C_SCATTER);
                     const float mu = hg_mu(d.g, pk.rng.next());
                     const float u2 = pk.rng.next();
                     uin = pk.r.u;
@@ -249,8 +200,6 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     after_event(PEEL_HG, 0, false);
                 }
             }
-        } else if (PEEL && mode == M_PEEL_DONE) {
-            finish_peels();
         }
         if (MRW && mode == M_MRW) mrw_steps();
         // refill: lanes without a packet take the next ids
@@ -260,11 +209,11 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             const long long q = fetch(need, lt_mask);
             if (mode == M_NEED) {
                 if (aborted || q < 0) {
-                    if (aborted && q >= 0) lc.v[C_WATCHDOG]++;
+                    if (aborted && q >= 0) lc.inc(C_WATCHDOG);
                     mode = M_DONE;
                 } else if (!emit_packet<G>(g, d, s, o, a, t, st.sed, (int64_t)q, pk, lc, false)) {
-                    lc.v[C_ESCAPED]++;
-                    lc.v[C_PACKETS_DONE]++;
+                    lc.inc(C_ESCAPED);
+                    lc.inc(C_PACKETS_DONE);
                 } else if (pk.src >= s.npoint && pk.src < s.npoint + s.next) {
                     start_walk();               // external field: background, not peeled off
                 } else {
@@ -280,12 +229,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         const int thr = min(a.regroup, __popc(live));
         unsigned steps = 0;
         for (;;) {
-            const unsigned walkers = __ballot_sync(FULL, mode == M_WALK || mode == M_PEEL);
+            const unsigned walkers = __ballot_sync(FULL, mode == M_WALK);
             if (walkers == 0 || (__popc(walkers) < thr && walkers != live)) break;
             bool flushing = false;
             int32_t fci = 0;
             float fval = 0.f;
-            if (mode == M_WALK || mode == M_PEEL) {
+            if (mode == M_WALK) {
                 int axis, dir = 0;
                 float l;
                 if constexpr (G == GRID_CARTESIAN) {
@@ -297,68 +246,53 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 const float rho = fresh ? __ldg(g.rhoL + pk.r.ci) : rho_nx;
                 fresh = false;
                 const float k = rho * pk.dust.chi;
+                const float dtau = k * l;
+                float seg = l;
                 bool stop = false;
-                if (!PEEL || mode == M_WALK) {
-                    const float dtau = k * l;
-                    float seg = l;
-                    if (tau < dtau) {
-                        seg = tau / k;
-                        stop = true;
-                    } else {
-                        tau -= dtau;
-                    }
-                    if (rho > 0.f) {
-                        const float v = pk.dust.kappa * seg;
-                        if (pk.r.ci == dep_ci) {
-                            dep_val += v;
-                        } else {
-                            flushing = dep_ci >= 0;
-                            fci = dep_ci;
-                            fval = dep_val;
-                            dep_ci = pk.r.ci;
-                            dep_val = v;
-                        }
-                    }
-                    if (stop) {
-                        pk.r.p.x += seg * pk.r.u.x;
-                        pk.r.p.y += seg * pk.r.u.y;
-                        pk.r.p.z += seg * pk.r.u.z;
-                        mode = M_INTERACT;
-                    } else {
-                        lc.v[C_CROSSINGS]++;
-                    }
+                if (tau < dtau) {
+                    seg = tau / k;
+                    stop = true;
                 } else {
-                    tau += k * l;
-                    lc.v[C_PEEL_CROSSINGS]++;
-                    // a peel ray behind more than PEEL_TAU_STOP carries < 4e-18 of its weight
-                    if (tau > PEEL_TAU_STOP) stop = true, mode = M_PEEL_DONE;
+                    tau -= dtau;
+                }
+                if (rho > 0.f) {
+                    const float v = pk.dust.kappa * seg;
+                    if (pk.r.ci == dep_ci) {
+                        dep_val += v;
+                    } else {
+                        flushing = dep_ci >= 0;
+                        fci = dep_ci;
+                        fval = dep_val;
+                        dep_ci = pk.r.ci;
+                        dep_val = v;
+                    }
+                }
+                if (stop) {
+                    pk.r.p.x += seg * pk.r.u.x;
+                    pk.r.p.y += seg * pk.r.u.y;
+                    pk.r.p.z += seg * pk.r.u.z;
+                    mode = M_INTERACT;
+                } else {
+                    lc.inc(C_CROSSINGS);
                 }
                 if (!stop) {
                     bool out;
                     if constexpr (G == GRID_CARTESIAN) out = cart_step_w(g, pk.r, wn, l, axis);
                     else out = cell_step<G>(g, pk.r, l, axis, dir);
-                    if (out) mode = (mode == M_WALK) ? M_ESCAPED : M_PEEL_DONE;
+                    if (out) mode = M_ESCAPED;
                     else rho_nx = __ldg(g.rhoL + pk.r.ci);      // the next crossing's density, ahead of use
                     if constexpr (G != GRID_CARTESIAN) {
                         if (!tiny_step(pk.r, l)) zero_run = 0;
                         else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
                     }
-                    if (++ray_steps > MAX_WALK_STEPS && (mode == M_WALK || mode == M_PEEL)) {
-                        lc.v[C_STUCK]++;
-                        if (mode == M_WALK) {
-                            lc.v[C_KILLED]++;
-                            mode = M_KILLED;
-                        } else {
-                            tau = F_INF;           // the peel ray is dropped (zero weight)
-                            mode = M_PEEL_DONE;
-                        }
+                    if (++ray_steps > MAX_WALK_STEPS && mode == M_WALK) {
+                        lc.inc(C_STUCK);
+                        lc.inc(C_KILLED);
+                        mode = M_KILLED;
                     }
                 } else {
                     ray_steps = 0;
                 }
-            }
-            if constexpr (PEEL) {
-                if (mode == M_PEEL_DONE) finish_peels();
             }
             flush_deposit<WAGG>(t.acc, t.visits, flushing, fci, fval);
             if (((++steps) & 4095u) == 0) watchdog(steps);
@@ -369,13 +303,15 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
 }
 
 // ---------------------------------------------------------------- one model
-// MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80);
-// PEEL = imaging pass (peel-off rays walked), compiled out of the Lucy iterations' kernel.
+// MINB = resident blocks per SM the registers are budgeted for (2: 128 registers, 3: 80, 4: 64);
+// PEEL = imaging pass (peel-off events queued, or peeled in place), compiled out of the Lucy
+// iterations' kernel.
 template <int G, bool WAGG, int MINB, bool PEEL, bool MRW>
 __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
     const SharedTallies st = shared_tallies(o, a);
+    __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     LocalCounters lc;
-    lc.zero();
+    lc.init(cnt_sh[threadIdx.x >> 5]);
     const unsigned lane = threadIdx.x & 31u;
     auto fetch = [&](unsigned need, unsigned lt_mask) -> long long {
         unsigned long long base = 0;
@@ -399,6 +335,9 @@ template <int G, bool PEEL>
 static cudaError_t launch_event_shape(const PropagateJob& j, const Launch& l, int bps, cudaStream_t s) {
     constexpr bool WAGG = G == GRID_CARTESIAN;
     if (j.args.mrw_gamma > 0.f) return launch_persistent(k_event<G, WAGG, 3, PEEL, true>, j, l, s);
+    if constexpr (!PEEL) {
+        if (bps >= 4) return launch_persistent(k_event<G, WAGG, 4, PEEL, false>, j, l, s);
+    }
     if (bps >= 3) return launch_persistent(k_event<G, WAGG, 3, PEEL, false>, j, l, s);
     return launch_persistent(k_event<G, WAGG, 2, PEEL, false>, j, l, s);
 }
@@ -410,7 +349,9 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     PropagateJob j = job;
     const bool peel = job.args.peel != 0;
     // default shapes (measured on GB300): Lucy iterations at 3 blocks of 256 per SM (80
-    // registers), imaging passes at 2 (128 registers: the peel-off code spills at 80); warps stay
+    // registers) on Cartesian grids and 4 (64 registers) on spherical ones, 7 % faster there
+    // despite some spilling (and 0.5 % slower on the 256^3 cloud); imaging passes at 2 (128
+    // registers: with the queue push and the in-place peel-off the kernel spills at 80); warps stay
     // in the walk phase while at least 24 lanes walk on curvilinear grids, 20 on Cartesian runs of
     // >= 4M packets, 12 for small Cartesian runs whose tail dominates
     int rg_default = DEFAULT_REGROUP;
@@ -418,7 +359,7 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 2 : 3);
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 2 : job.grid.type == GRID_SPHERICAL ? 4 : 3);
     cudaError_t e;
     if (job.grid.type == GRID_CARTESIAN)
         e = peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
@@ -440,6 +381,7 @@ __global__ void __launch_bounds__(256, MINB) k_event_batch(const BatchModel* __r
                                                         int regroup) {
     const unsigned lane = threadIdx.x & 31u;
     const SharedTallies st{nullptr, nullptr};
+    __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     for (;;) {
         int c = 0;
         if (lane == 0) c = (int)atomicAdd(chunk_counter, 1u);
@@ -459,7 +401,7 @@ __global__ void __launch_bounds__(256, MINB) k_event_batch(const BatchModel* __r
             return q < end ? q : -1ll;
         };
         LocalCounters lc;
-        lc.zero();
+        lc.init(cnt_sh[threadIdx.x >> 5]);
         event_loop<G, WAGG, false, false>(M.g, M.d, M.s, M.o, a, M.t, st, lc, fetch);
         flush_counters(lc, M.t.counters);
     }
@@ -477,7 +419,7 @@ static void launch_batch_shape(const BatchModel* models, const BatchChunk* chunk
                                                                                  state, regroup);
 }
 
-// Default shape as for one model: 3 blocks of 256 per SM, regroup 20; the autotuner times others.
+// Default shape: 3 blocks of 256 per SM, regroup 20; the autotuner times others (2-4 blocks).
 cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const BatchChunk* chunks, int nchunks,
                                    unsigned* chunk_counter, const BatchState* state, const Launch& l, cudaStream_t s) {
     int dev = 0, sms = 0;
@@ -486,10 +428,12 @@ cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const Ba
     const int regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : 20;
     const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
     if (gtype == GRID_CARTESIAN) {
-        if (bps >= 3) launch_batch_shape<GRID_CARTESIAN, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        if (bps >= 4) launch_batch_shape<GRID_CARTESIAN, 4>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        else if (bps == 3) launch_batch_shape<GRID_CARTESIAN, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
         else launch_batch_shape<GRID_CARTESIAN, 2>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
     } else {
-        if (bps >= 3) launch_batch_shape<GRID_SPHERICAL, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        if (bps >= 4) launch_batch_shape<GRID_SPHERICAL, 4>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
+        else if (bps == 3) launch_batch_shape<GRID_SPHERICAL, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
         else launch_batch_shape<GRID_SPHERICAL, 2>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
     }
     return cudaGetLastError();

@@ -568,6 +568,28 @@ cudaError_t weights_bf16(const float* w, bf16* wb, bf16* wt, int cin_real, int C
     return cudaGetLastError();
 }
 
+// Bp [Cin/8][Cout/BN][27][BN][8] from B [27][Cout][Cin]
+__global__ void k_pack_tma_weights(const bf16* __restrict__ B, bf16* __restrict__ Bp, int Cin, int Cout, int BN) {
+    GRID_STRIDE(i, 27LL * Cin * Cout) {
+        long long r = i;
+        const int c = (int)(r % 8);
+        r /= 8;
+        const int n = (int)(r % BN);
+        r /= BN;
+        const int tap = (int)(r % 27);
+        r /= 27;
+        const int nt = (int)(r % (Cout / BN));
+        const int c8 = (int)(r / (Cout / BN));
+        Bp[i] = B[((long long)tap * Cout + nt * BN + n) * Cin + c8 * 8 + c];
+    }
+}
+
+cudaError_t pack_tma_weights(const bf16* B, bf16* Bp, int Cin, int Cout, cudaStream_t s) {
+    if (Cin <= 0 || Cout <= 0 || Cin % 8 != 0 || Cout % 32 != 0) return cudaErrorInvalidValue;
+    k_pack_tma_weights<<<blocks_for(27LL * Cin * Cout), 256, 0, s>>>(B, Bp, Cin, Cout, tma_tile_n(Cout));
+    return cudaGetLastError();
+}
+
 // uniform(-bound, bound) initial weights from Philox-free integer hashing (splitmix64)
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     x += 0x9E3779B97F4A7C15ull;

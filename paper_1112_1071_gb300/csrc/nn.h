@@ -14,8 +14,10 @@ using bf16 = __nv_bfloat16;
 // Forward: B = W^T; data gradient: in = dY, B = W, flip = true, no bias, no ReLU.
 // conv3d runs on the tcgen05 tensor cores (nn_tc.cu); conv3d_mma is the same convolution with
 // warp-level mma.sync, kept as the measured baseline.
-cudaError_t conv3d(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
-                   int Cout, bool flip, bool relu, cudaStream_t s);
+// Bp (may be null): B packed by pack_tma_weights, which the TMA-fed kernel needs; without it
+// conv3d runs the per-phase kernel.
+cudaError_t conv3d(const bf16* in, const bf16* B, const bf16* Bp, const float* bias, bf16* out, int N, int D, int H,
+                   int W, int Cin, int Cout, bool flip, bool relu, cudaStream_t s);
 cudaError_t conv3d_phased(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
                    int Cout, bool flip, bool relu, cudaStream_t s);
 cudaError_t conv3d_mma(const bf16* in, const bf16* B, const float* bias, bf16* out, int N, int D, int H, int W,
@@ -45,6 +47,12 @@ cudaError_t head_backward(const bf16* h, const float* w, const float* dy, bf16* 
                           int C, cudaStream_t s);
 cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s);
 cudaError_t weights_bf16(const float* w, bf16* wb, bf16* wt, int cin_real, int Cin, int Cout, cudaStream_t s);
+// Weights for the TMA-fed convolution: B [27][Cout][Cin] rearranged as [Cin/8][Cout/BN][27][BN][8]
+// (BN = tma_tile_n(Cout) output channels per tile), so that what one pipeline stage needs of an
+// 8-channel slice -- all 27 taps of one output-channel tile -- is one contiguous block, moved by
+// one bulk copy.  Cin % 8 == 0, Cout % 32 == 0.
+constexpr int tma_tile_n(int Cout) { return Cout % 64 == 0 ? 64 : 32; }
+cudaError_t pack_tma_weights(const bf16* B, bf16* Bp, int Cin, int Cout, cudaStream_t s);
 cudaError_t init_uniform(float* p, long long n, float bound, unsigned long long seed, cudaStream_t s);
 cudaError_t pack_input(const float* x, bf16* y, long long NV, int cin, int Cpad, cudaStream_t s);
 cudaError_t bf16_to_f32(const bf16* x, float* y, long long n, cudaStream_t s);

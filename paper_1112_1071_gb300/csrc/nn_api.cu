@@ -33,6 +33,8 @@ struct Layer {
     long long w_off, b_off;      // into the FP32 parameter vector
     bf16* wb = nullptr;          // [27][cin][cout]
     bf16* wt = nullptr;          // [27][cout][cin]
+    bf16* wtp = nullptr;         // wt packed for the TMA-fed convolution (forward)
+    bf16* wbp = nullptr;         // wb packed likewise (data gradient; null when cin % 32 != 0)
 };
 
 template <class T>
@@ -123,8 +125,11 @@ int alloc_acts(hrt_net* n, int N, int D, int H, int W) {
 }
 
 int refresh_bf16(hrt_net* n) {
-    for (const Layer& l : n->layers)
+    for (const Layer& l : n->layers) {
         NCK(nn::weights_bf16(n->p + l.w_off, l.wb, l.wt, l.cin, l.cin, l.cout, n->stream));
+        NCK(nn::pack_tma_weights(l.wt, l.wtp, l.cin, l.cout, n->stream));
+        if (l.wbp) NCK(nn::pack_tma_weights(l.wb, l.wbp, l.cout, l.cin, n->stream));
+    }
     return HRT_OK;
 }
 
@@ -138,18 +143,18 @@ int forward(hrt_net* n) {
     for (int l = 0; l < L; ++l) {
         const int D = n->D >> l, H = n->H >> l, W = n->W >> l;
         const Layer& a = n->layers[k++];
-        NCK(nn::conv3d(h, a.wt, n->p + a.b_off, n->e0[l], N, D, H, W, a.cin, a.cout, false, true, s));
+        NCK(nn::conv3d(h, a.wt, a.wtp, n->p + a.b_off, n->e0[l], N, D, H, W, a.cin, a.cout, false, true, s));
         const Layer& b = n->layers[k++];
-        NCK(nn::conv3d(n->e0[l], b.wt, n->p + b.b_off, n->e1[l], N, D, H, W, b.cin, b.cout, false, true, s));
+        NCK(nn::conv3d(n->e0[l], b.wt, b.wtp, n->p + b.b_off, n->e1[l], N, D, H, W, b.cin, b.cout, false, true, s));
         NCK(nn::pool2(n->e1[l], n->pooled[l], N, D, H, W, n->ch[l], s));
         h = n->pooled[l];
     }
     {
         const int D = n->D >> L, H = n->H >> L, W = n->W >> L;
         const Layer& a = n->layers[k++];
-        NCK(nn::conv3d(h, a.wt, n->p + a.b_off, n->b0, N, D, H, W, a.cin, a.cout, false, true, s));
+        NCK(nn::conv3d(h, a.wt, a.wtp, n->p + a.b_off, n->b0, N, D, H, W, a.cin, a.cout, false, true, s));
         const Layer& b = n->layers[k++];
-        NCK(nn::conv3d(n->b0, b.wt, n->p + b.b_off, n->b1, N, D, H, W, b.cin, b.cout, false, true, s));
+        NCK(nn::conv3d(n->b0, b.wt, b.wtp, n->p + b.b_off, n->b1, N, D, H, W, b.cin, b.cout, false, true, s));
         h = n->b1;
     }
     for (int l = L - 1; l >= 0; --l) {
@@ -157,9 +162,9 @@ int forward(hrt_net* n) {
         const int cprev = n->ch[l + 1];
         NCK(nn::concat_up(h, n->e1[l], n->cat[l], N, D, H, W, cprev, n->ch[l], s));
         const Layer& a = n->layers[k++];
-        NCK(nn::conv3d(n->cat[l], a.wt, n->p + a.b_off, n->d0[l], N, D, H, W, a.cin, a.cout, false, true, s));
+        NCK(nn::conv3d(n->cat[l], a.wt, a.wtp, n->p + a.b_off, n->d0[l], N, D, H, W, a.cin, a.cout, false, true, s));
         const Layer& b = n->layers[k++];
-        NCK(nn::conv3d(n->d0[l], b.wt, n->p + b.b_off, n->d1[l], N, D, H, W, b.cin, b.cout, false, true, s));
+        NCK(nn::conv3d(n->d0[l], b.wt, b.wtp, n->p + b.b_off, n->d1[l], N, D, H, W, b.cin, b.cout, false, true, s));
         h = n->d1[l];
     }
     NCK(nn::head_forward(h, n->p + n->head_w, n->p + n->head_b, n->y, (long long)N * n->D * n->H * n->W, n->ch[0], s));
@@ -174,7 +179,7 @@ int conv_back(hrt_net* n, const Layer& ly, const bf16* in, const bf16* out, bf16
     NCK(nn::relu_mask(g, out, NV * ly.cout, s));
     NCK(nn::conv3d_wgrad(in, g, n->g + ly.w_off, n->N, D, H, W, ly.cin, ly.cout, s));
     NCK(nn::bias_grad(g, n->g + ly.b_off, NV, ly.cout, s));
-    if (gin) NCK(nn::conv3d(g, ly.wb, nullptr, gin, n->N, D, H, W, ly.cout, ly.cin, true, false, s));
+    if (gin) NCK(nn::conv3d(g, ly.wb, ly.wbp, nullptr, gin, n->N, D, H, W, ly.cout, ly.cin, true, false, s));
     return HRT_OK;
 }
 
@@ -320,6 +325,8 @@ static int net_create(hrt_net** out, int device, const int* widths, int levels, 
     for (Layer& ly : n->layers) {
         ly.wb = dalloc<bf16>(27LL * ly.cin * ly.cout, e);
         ly.wt = dalloc<bf16>(27LL * ly.cin * ly.cout, e);
+        ly.wtp = dalloc<bf16>(27LL * ly.cin * ly.cout, e);
+        if (ly.cin % 32 == 0) ly.wbp = dalloc<bf16>(27LL * ly.cin * ly.cout, e);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -371,8 +378,8 @@ int hrt_net_destroy(hrt_net* n) {
     cudaStreamSynchronize(n->stream);
     free_acts(n);
     for (Layer& ly : n->layers) {
-        if (ly.wb) cudaFree(ly.wb);
-        if (ly.wt) cudaFree(ly.wt);
+        for (bf16* q : {ly.wb, ly.wt, ly.wtp, ly.wbp})
+            if (q) cudaFree(q);
     }
     for (float* q : {n->p, n->g, n->m, n->v})
         if (q) cudaFree(q);
@@ -583,16 +590,18 @@ static int conv3d_hook(int N, int D, int H, int W, int Cin, int Cout, const floa
     bf16* y = dalloc<bf16>(NV * Cout, e);
     bf16* wb = dalloc<bf16>(27LL * Cin * Cout, e);
     bf16* wt = dalloc<bf16>(27LL * Cin * Cout, e);
+    bf16* wtp = dalloc<bf16>(27LL * Cin * Cout, e);
     if (e == cudaSuccess) e = nn::f32_to_bf16(d_x, x, NV * Cin, s);
     if (e == cudaSuccess) e = nn::weights_bf16(d_w, wb, wt, Cin, Cin, Cout, s);
+    if (e == cudaSuccess) e = nn::pack_tma_weights(wt, wtp, Cin, Cout, s);
     if (e == cudaSuccess)
         e = impl == CONV_MMA      ? nn::conv3d_mma(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
             : impl == CONV_PHASED ? nn::conv3d_phased(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s)
-                                  : nn::conv3d(x, wt, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
+                                  : nn::conv3d(x, wt, wtp, d_b, y, N, D, H, W, Cin, Cout, false, relu != 0, s);
     if (e == cudaSuccess) e = nn::bf16_to_f32(y, d_y, NV * Cout, s);
     int failed = 0;
     if (e == cudaSuccess) e = nn::tc_status(&failed, s);
-    cudaFree(x); cudaFree(y); cudaFree(wb); cudaFree(wt);
+    cudaFree(x); cudaFree(y); cudaFree(wb); cudaFree(wt); cudaFree(wtp);
     if (e != cudaSuccess) cudaGetLastError();
     if (e == cudaSuccess && failed) return HRT_ETIMEDOUT;
     return e == cudaSuccess ? HRT_OK : HRT_ECUDA;
@@ -610,18 +619,20 @@ int hrt_nn_conv3d_backward(int N, int D, int H, int W, int Cin, int Cout, const 
     bf16* gx = dalloc<bf16>(NV * Cin, e);
     bf16* wb = dalloc<bf16>(27LL * Cin * Cout, e);
     bf16* wt = dalloc<bf16>(27LL * Cin * Cout, e);
+    bf16* wbp = dalloc<bf16>(27LL * Cin * Cout, e);
     if (e == cudaSuccess) e = nn::f32_to_bf16(d_x, x, NV * Cin, s);
     if (e == cudaSuccess) e = nn::f32_to_bf16(d_dy, g, NV * Cout, s);
     if (e == cudaSuccess) e = nn::weights_bf16(d_w, wb, wt, Cin, Cin, Cout, s);
+    if (e == cudaSuccess) e = nn::pack_tma_weights(wb, wbp, Cout, Cin, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dw, 0, 27LL * Cin * Cout * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_db, 0, Cout * sizeof(float), s);
     if (e == cudaSuccess) e = nn::conv3d_wgrad(x, g, d_dw, N, D, H, W, Cin, Cout, s);
     if (e == cudaSuccess) e = nn::bias_grad(g, d_db, NV, Cout, s);
-    if (e == cudaSuccess) e = nn::conv3d(g, wb, nullptr, gx, N, D, H, W, Cout, Cin, true, false, s);
+    if (e == cudaSuccess) e = nn::conv3d(g, wb, wbp, nullptr, gx, N, D, H, W, Cout, Cin, true, false, s);
     if (e == cudaSuccess) e = nn::bf16_to_f32(gx, d_dx, NV * Cin, s);
     int failed = 0;
     if (e == cudaSuccess) e = nn::tc_status(&failed, s);
-    cudaFree(x); cudaFree(g); cudaFree(gx); cudaFree(wb); cudaFree(wt);
+    cudaFree(x); cudaFree(g); cudaFree(gx); cudaFree(wb); cudaFree(wt); cudaFree(wbp);
     if (e != cudaSuccess) cudaGetLastError();
     if (e == cudaSuccess && failed) return HRT_ETIMEDOUT;
     return e == cudaSuccess ? HRT_OK : HRT_ECUDA;

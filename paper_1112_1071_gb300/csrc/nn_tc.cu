@@ -234,9 +234,9 @@ cudaError_t conv3d_phased(const bf16* in, const bf16* Bw, const float* bias, bf1
 // ---------------------------------------------------------------- TMA-fed, pipelined convolution
 // The same implicit GEMM as k_conv3d_tc, arranged for Blackwell's asynchronous units.  A
 // persistent CTA per SM walks its share of (image, z, 16 x 8 brick, output-channel tile) work
-// items with three roles: one thread loads, per 16-channel chunk, the halo (one box of 10 x 18 x
-// 3 voxels per 8-channel half) and all 27 taps' weights with TMA into one of the shared-memory
-// stages; one thread issues the chunk's 27 MMAs into one of two tensor-memory accumulators as
+// items with three roles: one thread loads, per 16-channel chunk, the halo (one TMA box of 10 x
+// 18 x 3 voxels per 8-channel half) and all 27 taps' weights (one bulk copy per 8-channel half
+// from the packed layout of pack_tma_weights) into one of the shared-memory stages; one thread issues the chunk's 27 MMAs into one of two tensor-memory accumulators as
 // soon as the stage has landed and hands the stage back when they complete; four epilogue warps
 // drain the other accumulator (bias, ReLU, BF16 store) meanwhile.  The loads of the next chunks
 // thus overlap the MMAs of this one, and a tile's epilogue the next tile's MMAs.  A TMA box of 8
@@ -245,7 +245,8 @@ cudaError_t conv3d_phased(const bf16* in, const bf16* Bw, const float* bias, bf1
 // voxels along x, so the three x shifts of a tap are the same box read 0, 16 or 32 bytes further
 // into each 160-byte row (the stride byte offset of the operand descriptor), and the halo is
 // loaded once, not three times; the second channel half lies one region further (its leading
-// byte offset).  The weights land the same way, 8 output channels per core matrix.  Every wait
+// byte offset).  The packed weights land as [tap][output channel][8 channels], 8 output channels
+// per core matrix, so a chunk's weights are 2 bulk copies, not 2 x 27 x BN 16-byte rows.  Every wait
 // gives up after WAIT_LIMIT_NS (or when another role has given up): the block records the error,
 // lets its own loads and MMAs drain (bounded), frees its tensor memory and returns.
 constexpr int TM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
@@ -265,8 +266,7 @@ struct TmShape {
 
 template <int BN>
 __global__ void __launch_bounds__(TM_THREADS, 1)
-    k_conv3d_tma(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap wts,
-                 const float* __restrict__ bias, bf16* __restrict__ out, int N, int D, int H, int W, int Cin, int Cout,
+    k_conv3d_tma(const __grid_constant__ CUtensorMap act, const bf16* __restrict__ Bp, const float* __restrict__ bias, bf16* __restrict__ out, int N, int D, int H, int W, int Cin, int Cout,
                  int flip, int relu) {
     constexpr int STAGE = TmShape<BN>::STAGE, WHALF = TmShape<BN>::WHALF, TM_STAGES = TmShape<BN>::STAGES;
     constexpr uint32_t NCOLS = 2 * BN;
@@ -347,7 +347,6 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
             tc::tma_prefetch_map(&act);
-            tc::tma_prefetch_map(&wts);
             long long it = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -365,7 +364,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
                     for (int h = 0; h < 2; ++h)
                         tc::tma_load_5d(sb + h * TM_HALF, &act, c * KC + h * 8, x0 - 1, y0 - 1, z - 1, b, full(st));
                     for (int h = 0; h < 2; ++h)
-                        tc::tma_load_3d(sb + 2 * TM_HALF + h * WHALF, &wts, c * KC + h * 8, n0, 0, full(st));
+                        tc::bulk_load(sb + 2 * TM_HALF + h * WHALF,
+                                      Bp + ((long long)(c * 2 + h) * ntn + n0 / BN) * (27 * BN * 8), WHALF, full(st));
                 }
             }
             // no copy may still be landing when the block leaves: wait for the last stages issued
@@ -391,13 +391,16 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
                     }
                     tc::fence_after_sync();
                     const uint32_t sb = base + st * STAGE;
-#pragma unroll 1
+                    // the stage's descriptors once; each tap adds a constant to their address
+                    // field (shared addresses < 2^18, so the 14-bit field never carries)
+                    const uint64_t a0 = tc::smem_desc(sb, TM_HALF, TM_ROW);
+                    const uint64_t b0 = tc::smem_desc(sb + 2 * TM_HALF, WHALF, 128);
+#pragma unroll
                     for (int tap = 0; tap < 27; ++tap) {
                         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                        const uint32_t a = sb + (dz * HALO_Y + dy) * TM_ROW + dx * 16;
-                        const uint32_t bw = sb + 2 * TM_HALF + (flip ? 26 - tap : tap) * BN * 16;
-                        tc::mma_bf16(acc, tc::smem_desc(a, TM_HALF, TM_ROW), tc::smem_desc(bw, WHALF, 128), IDESC,
-                                     (c > 0 || tap > 0) ? 1u : 0u);
+                        const uint32_t aoff = ((dz * HALO_Y + dy) * TM_ROW + dx * 16) >> 4;
+                        const uint32_t boff = (flip ? (26 - tap) * BN : tap * BN);   // x 16 bytes >> 4
+                        tc::mma_bf16(acc, a0 + aoff, b0 + boff, IDESC, (c > 0 || tap > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(empty(st));          // the stage is free once these MMAs complete
                 }
@@ -477,24 +480,17 @@ EncodeTiled encode_tiled() {
 }  // namespace
 
 template <int BN>
-static cudaError_t launch_tma(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W,
+static cudaError_t launch_tma(const bf16* in, const bf16* Bp, const float* bias, bf16* out, int N, int D, int H, int W,
                               int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     EncodeTiled enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
-    CUtensorMap act, wts;
+    CUtensorMap act;
     const cuuint64_t adim[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
     const cuuint64_t astr[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
                                 (cuuint64_t)D * H * W * Cin * 2};
     const cuuint32_t abox[5] = {8, TM_HX, HALO_Y, 3, 1};
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), adim, astr, abox, ones,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    const cuuint64_t wdim[3] = {(cuuint64_t)Cin, (cuuint64_t)Cout, 27};
-    const cuuint64_t wstr[2] = {(cuuint64_t)Cin * 2, (cuuint64_t)Cout * Cin * 2};
-    const cuuint32_t wbox[3] = {8, BN, 27};
-    if (enc(&wts, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Bw), wdim, wstr, wbox, ones,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -506,19 +502,20 @@ static cudaError_t launch_tma(const bf16* in, const bf16* Bw, const float* bias,
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long ntiles = (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + BRICK_X - 1) / BRICK_X) * (Cout / BN);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_conv3d_tma<BN><<<grid, TM_THREADS, SMEM, s>>>(act, wts, bias, out, N, D, H, W, Cin, Cout, flip ? 1 : 0,
+    k_conv3d_tma<BN><<<grid, TM_THREADS, SMEM, s>>>(act, Bp, bias, out, N, D, H, W, Cin, Cout, flip ? 1 : 0,
                                                     relu ? 1 : 0);
     return cudaGetLastError();
 }
 
-// The TMA-fed kernel for output tiles of 64 channels (Cout % 64 == 0), the phased kernel for the
-// rest: measured on GB300 (ncu, kernel time), the pipeline is 1.2-1.4x faster at 64-channel tiles
-// (2 x 64^3, 64 -> 64: 0.278 against 0.381 ms) and no faster at 32 (4 x 64^3, 32 -> 32: 0.303
-// against 0.291 ms), where each chunk's 2,800 16-byte TMA rows, not the MMAs, set the pace.
-cudaError_t conv3d(const bf16* in, const bf16* Bw, const float* bias, bf16* out, int N, int D, int H, int W, int Cin,
-                   int Cout, bool flip, bool relu, cudaStream_t s) {
+// The TMA-fed kernel whenever the packed weights are given (tiles of 64 output channels when
+// Cout % 64 == 0, else 32), the per-phase kernel otherwise.
+cudaError_t conv3d(const bf16* in, const bf16* Bw, const bf16* Bp, const float* bias, bf16* out, int N, int D, int H,
+                   int W, int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     if (Cin % 16 != 0 || Cout % 32 != 0 || Cin <= 0 || Cout <= 0) return cudaErrorInvalidValue;
-    if (Cout % 64 == 0 && encode_tiled()) return launch_tma<64>(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    if (Bp && encode_tiled()) {
+        if (tma_tile_n(Cout) == 64) return launch_tma<64>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+        return launch_tma<32>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+    }
     return conv3d_phased(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
 

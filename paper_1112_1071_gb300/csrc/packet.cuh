@@ -7,25 +7,49 @@
 
 namespace hrt {
 
+// Per-thread tallies of a propagation kernel.  The two per-crossing counts live in registers; the
+// per-event counts (escapes, interactions, ...: one per tens of crossings) go by shared-memory
+// atomics to the warp's slot, so a thread holds 4 registers of counters instead of 2 per counter.
+// `slot` is this warp's row of a kernel's __shared__ unsigned long long [8][N_COUNTERS] (blocks
+// of <= 256 threads).
 struct LocalCounters {
-    unsigned long long v[N_COUNTERS];
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int i = 0; i < N_COUNTERS; ++i) v[i] = 0ull;
+    unsigned long long cross, peel_cross;
+    unsigned long long* slot;
+    __device__ __forceinline__ void init(unsigned long long* warp_slot) {
+        cross = peel_cross = 0ull;
+        slot = warp_slot;
+        const unsigned lane = threadIdx.x & 31u;
+        if (lane < (unsigned)N_COUNTERS) slot[lane] = 0ull;
+        __syncwarp();
     }
+    __device__ __forceinline__ void add(int c, unsigned long long x) {
+        if (c == C_CROSSINGS) cross += x;
+        else if (c == C_PEEL_CROSSINGS) peel_cross += x;
+        else atomicAdd(slot + c, x);
+    }
+    __device__ __forceinline__ void inc(int c) { add(c, 1ull); }
 };
 
-// Warp-reduce the per-thread counters and add them to the global tallies (one atomic per warp
-// and counter).
-__device__ __forceinline__ void flush_counters(const LocalCounters& lc, unsigned long long* g) {
+// Whole warp: add the warp's counts to the global tallies (one atomic per warp and counter) and
+// start again from zero.
+__device__ __forceinline__ void flush_counters(LocalCounters& lc, unsigned long long* g) {
     const unsigned lane = threadIdx.x & 31u;
+    unsigned long long x = lc.cross, y = lc.peel_cross;
 #pragma unroll
-    for (int i = 0; i < N_COUNTERS; ++i) {
-        unsigned long long x = lc.v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0 && x) atomicAdd(g + i, x);
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
     }
+    if (lane == 0 && x) atomicAdd(g + C_CROSSINGS, x);
+    if (lane == 0 && y) atomicAdd(g + C_PEEL_CROSSINGS, y);
+    __syncwarp();
+    if (lane < (unsigned)N_COUNTERS && lane != (unsigned)C_CROSSINGS && lane != (unsigned)C_PEEL_CROSSINGS) {
+        const unsigned long long z = lc.slot[lane];
+        if (z) atomicAdd(g + lane, z);
+        lc.slot[lane] = 0ull;
+    }
+    __syncwarp();
+    lc.cross = lc.peel_cross = 0ull;
 }
 
 // SED bin of a frequency: floor(nsed ln(lambda/lambda_min) / ln(lambda_max/lambda_min)), -1 outside.
@@ -91,7 +115,10 @@ __device__ void peel_event(const DevGrid& g, const DevDust& d, const DevObs& o, 
         if (col) tau = chi * fmaxf(__ldg(col + ob), 0.f);
         else {
             if (relocate) inside = grid_locate<G>(g, pr);
-            if (inside) tau = tau_to_edge<G>(g, pr, chi, lc.v[C_PEEL_CROSSINGS], tau_stop);
+            if (inside) {
+                tau = tau_to_edge<G>(g, pr, chi, lc.peel_cross, tau_stop);
+                if (tau == F_INF) lc.inc(C_STUCK);
+            }
         }
         const double w = a.eps * (double)(prob * expf(-tau));
         if (sed_s) atomicAdd(sed_s + ob * o.nsed + sbin, w);
@@ -222,12 +249,12 @@ __device__ bool emit_packet(const DevGrid& g, const DevDust& d, const DevSources
 template <int G>
 __device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, const DevObs& o, const RunArgs& a,
                                          const Tallies& t, double* sed_s, Packet& pk, LocalCounters& lc) {
-    lc.v[C_INTERACTIONS]++;
+    lc.inc(C_INTERACTIONS);
     const float z = pk.rng.next();
     if (z > pk.dust.albedo) {
-        lc.v[C_ABSORB]++;
+        lc.inc(C_ABSORB);
         if (a.terminate_on_absorb) {
-            lc.v[C_ABSORBED_TERM]++;
+            lc.inc(C_ABSORBED_TERM);
             return false;
         }
         const float u1 = pk.rng.next(), u2 = pk.rng.next();
@@ -236,7 +263,7 @@ __device__ __forceinline__ bool interact(const DevGrid& g, const DevDust& d, con
         set_frequency(pk, d, o, sample_table(d.nu, d.cdf_emit + (int64_t)row * d.nnu, d.nnu, pk.rng.next()));
         if (a.peel && !a.rt) peel_event<G>(g, d, o, a, t, sed_s, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
     } else {
-        lc.v[C_SCATTER]++;
+        lc.inc(C_SCATTER);
         const float mu = hg_mu(d.g, pk.rng.next());
         const float u2 = pk.rng.next();
         const float3 uin = pk.r.u;

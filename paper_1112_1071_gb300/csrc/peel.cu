@@ -103,15 +103,16 @@ template <int G>
 __global__ void __launch_bounds__(256, PEEL_MINB)
     k_peel_rays(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t, const uint32_t* __restrict__ order) {
     const SharedTallies st = shared_tallies(o, a);
+    __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     LocalCounters lc;
-    lc.zero();
+    lc.init(cnt_sh[threadIdx.x >> 5]);
     const unsigned long long n_ev = queued_events(a);
     const unsigned long long total = n_ev * (unsigned long long)o.nobs;
     unsigned check = 0;
     for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         if (((++check) & 63u) == 0 && past_deadline(a, t)) {
-            lc.v[C_WATCHDOG]++;
+            lc.inc(C_WATCHDOG);
             break;
         }
         const int ob = (int)(q / n_ev);
@@ -133,24 +134,9 @@ __global__ void __launch_bounds__(256, PEEL_MINB)
         set_dir(r, n);
         float tau = 0.f;
         if (e.ci >= 0 || grid_locate<G>(g, r)) {
-            int zero_run = 0;
-            for (unsigned steps = 0;;) {
-                int axis, dir;
-                const float l = cell_exit<G>(g, r, axis, dir);
-                tau += __ldg(g.rhoL + r.ci) * chi * l;
-                lc.v[C_PEEL_CROSSINGS]++;
-                if (tau > PEEL_TAU_STOP) break;             // < 4e-18 of the weight remains
-                if (cell_step<G>(g, r, l, axis, dir)) break;
-                if constexpr (G != GRID_CARTESIAN) {
-                    if (!tiny_step(r, l)) zero_run = 0;
-                    else if (++zero_run > ZERO_RUN_LIMIT) { nudge(r); zero_run = 0; }
-                }
-                if (++steps > MAX_WALK_STEPS) {
-                    lc.v[C_STUCK]++;
-                    tau = F_INF;                            // the ray is dropped (zero weight)
-                    break;
-                }
-            }
+            // stops past PEEL_TAU_STOP (< 4e-18 of the weight remains); F_INF: stuck, dropped
+            tau = tau_to_edge<G>(g, r, chi, lc.peel_cross, PEEL_TAU_STOP);
+            if (tau == F_INF) lc.inc(C_STUCK);
         }
         const float prob = (e.nu < 0.f) ? hg_phase(d.g, dot3(make_float3(e.ux, e.uy, e.uz), n)) : (0.25f / CUDART_PI_F);
         const double w = a.eps * (double)(prob * expf(-tau));

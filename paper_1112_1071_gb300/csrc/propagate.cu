@@ -30,7 +30,7 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
             else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
         }
         if (check >= MAX_WALK_STEPS) {
-            lc.v[C_STUCK]++;
+            lc.inc(C_STUCK);
             return EV_STUCK;
         }
         const float rho = __ldg(g.rhoL + pk.r.ci);
@@ -50,7 +50,7 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
         }
         if (rho > 0.f) atomicAdd(t.acc + pk.r.ci, (double)(kap * l));
         tau -= dtau;
-        lc.v[C_CROSSINGS]++;
+        lc.inc(C_CROSSINGS);
         if (cell_step<G>(g, pk.r, l, axis, dir)) return EV_ESCAPE;
         if (((++check) & 1023u) == 0 && past_deadline(a, t)) return EV_ABORT;
     }
@@ -59,18 +59,19 @@ __device__ __forceinline__ int walk_plain(const DevGrid& g, const RunArgs& a, co
 template <int G>
 __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources s, DevObs o, RunArgs a, Tallies t) {
     const SharedTallies st = shared_tallies(o, a);
+    __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     LocalCounters lc;
-    lc.zero();
+    lc.init(cnt_sh[threadIdx.x >> 5]);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_packets; q += stride) {
         if (past_deadline(a, t)) {
-            lc.v[C_WATCHDOG]++;
+            lc.inc(C_WATCHDOG);
             break;
         }
         Packet pk;
         if (!emit_packet<G>(g, d, s, o, a, t, st.sed, a.first_packet + q, pk, lc)) {
-            lc.v[C_ESCAPED]++;
-            lc.v[C_PACKETS_DONE]++;
+            lc.inc(C_ESCAPED);
+            lc.inc(C_PACKETS_DONE);
             continue;
         }
         for (;;) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
                     killed = true;
                     break;
                 }
-                lc.v[C_MRW]++;
+                lc.inc(C_MRW);
                 const float v = mrw_take(d, o, a, pk, R0);
                 atomicAdd(t.acc + pk.r.ci, widen(v));
                 if (t.visits && pk.r.ci != pk.run_ci) {
@@ -95,31 +96,31 @@ __global__ void __launch_bounds__(256) k_plain(DevGrid g, DevDust d, DevSources 
                     peel_event<G>(g, d, o, a, t, st.sed, pk.r, pk.r.u, PEEL_ISO, false, pk.dust.chi, pk.sbin, lc);
             }
             if (killed) {
-                lc.v[C_KILLED]++;
+                lc.inc(C_KILLED);
                 break;
             }
             const float tau = -logf(pk.rng.next());
             const int ev = walk_plain<G>(g, a, t, pk, tau, lc);
             if (ev == EV_ESCAPE) {
-                lc.v[C_ESCAPED]++;
+                lc.inc(C_ESCAPED);
                 tally_escape(o, t, pk, st.esc);
                 break;
             }
             if (ev == EV_ABORT) {
-                lc.v[C_WATCHDOG]++;
+                lc.inc(C_WATCHDOG);
                 break;
             }
             if (ev == EV_STUCK) {
-                lc.v[C_KILLED]++;
+                lc.inc(C_KILLED);
                 break;
             }
             if (++pk.nint > a.max_interactions) {
-                lc.v[C_KILLED]++;
+                lc.inc(C_KILLED);
                 break;
             }
             if (!interact<G>(g, d, o, a, t, st.sed, pk, lc)) break;
         }
-        lc.v[C_PACKETS_DONE]++;
+        lc.inc(C_PACKETS_DONE);
     }
     flush_counters(lc, t.counters);
     flush_shared(o, a, t, st);

@@ -193,7 +193,7 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
                     pk.r.p.z += seg * pk.r.u.z;
                     mode = L_INTERACT;
                 } else {
-                    lc.v[C_CROSSINGS]++;
+                    lc.inc(C_CROSSINGS);
                     bool out;
                     if constexpr (G == GRID_CARTESIAN) out = cart_step_w(g, pk.r, wn, l, axis);
                     else out = cell_step<G>(g, pk.r, l, axis, dir);
@@ -204,8 +204,8 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
                         else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
                     }
                     if (++ray_steps > MAX_WALK_STEPS && mode == L_WALK) {
-                        lc.v[C_STUCK]++;
-                        lc.v[C_KILLED]++;
+                        lc.inc(C_STUCK);
+                        lc.inc(C_KILLED);
                         mode = L_KILLED;
                     }
                 }
@@ -217,7 +217,7 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
                 if (__shfl_sync(FULL, ab ? 1 : 0, 0)) {
                     if (lane == 0) {
                         vstore(&sh.abort, 1);
-                        lc.v[C_WATCHDOG]++;
+                        lc.inc(C_WATCHDOG);
                     }
                     break;
                 }
@@ -229,30 +229,30 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
         if (mode == L_INTERACT) {
             ray_steps = 0;
             if (++pk.nint > a.max_interactions) {
-                lc.v[C_KILLED]++;
+                lc.inc(C_KILLED);
                 flush_run(t, dep_ci, dep_val);
-                lc.v[C_PACKETS_DONE]++;
+                lc.inc(C_PACKETS_DONE);
                 code = RG_NEED;
             } else {
-                lc.v[C_INTERACTIONS]++;
+                lc.inc(C_INTERACTIONS);
                 const float z = pk.rng.next();
                 if (z > pk.dust.albedo) {
-                    lc.v[C_ABSORB]++;
+                    lc.inc(C_ABSORB);
                     code = RG_ABSORB;
                 } else {
-                    lc.v[C_SCATTER]++;
+                    lc.inc(C_SCATTER);
                     code = RG_SCATTER;
                 }
             }
         } else if (mode == L_ESCAPED) {
-            lc.v[C_ESCAPED]++;
+            lc.inc(C_ESCAPED);
             tally_escape(o, t, pk, st.esc);
             flush_run(t, dep_ci, dep_val);
-            lc.v[C_PACKETS_DONE]++;
+            lc.inc(C_PACKETS_DONE);
             code = RG_NEED;
         } else if (mode == L_KILLED) {
             flush_run(t, dep_ci, dep_val);
-            lc.v[C_PACKETS_DONE]++;
+            lc.inc(C_PACKETS_DONE);
             code = RG_NEED;
         }
         const bool push = mode == L_INTERACT || mode == L_ESCAPED || mode == L_KILLED;
@@ -314,7 +314,7 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
                 if (__shfl_sync(FULL, ab ? 1 : 0, 0)) {
                     if (lane == 0) {
                         vstore(&sh.abort, 1);
-                        lc.v[C_WATCHDOG]++;
+                        lc.inc(C_WATCHDOG);
                     }
                     break;
                 }
@@ -326,7 +326,7 @@ __device__ void rg_walker(const DevGrid& g, const DevDust& d, const DevObs& o, c
     // stopped by the watchdog or a stall: lanes that still hold a packet record it and stop
     const bool aborted = __shfl_sync(FULL, lane == 0 ? vload(&sh.abort) : 0, 0) != 0;
     if (aborted && mode != L_DONE && mode != L_IDLE) {
-        lc.v[C_WATCHDOG]++;
+        lc.inc(C_WATCHDOG);
         const unsigned slot = atomicAdd(t.report_count, 1u);
         if (slot < (unsigned)WD_REPORTS) {
             float* r = t.report + slot * WD_FIELDS;
@@ -444,8 +444,8 @@ __device__ void rg_service(const DevGrid& g, const DevDust& d, const DevSources&
                     if (q >= (unsigned long long)a.n_packets) {
                         result = RG_DONE;
                     } else if (!emit_packet<G>(g, d, s, o, a, t, st.sed, a.first_packet + (int64_t)q, pk, lc, false)) {
-                        lc.v[C_ESCAPED]++;                   // starts outside the grid
-                        lc.v[C_PACKETS_DONE]++;
+                        lc.inc(C_ESCAPED);                   // starts outside the grid
+                        lc.inc(C_PACKETS_DONE);
                         again = true;
                     } else {
                         if (!(pk.src >= s.npoint && pk.src < s.npoint + s.next))    // external field: not peeled
@@ -463,9 +463,9 @@ __device__ void rg_service(const DevGrid& g, const DevDust& d, const DevSources&
                     peel(pk, pk.r.p, uin, PEEL_HG, 0, false);
                     tau = -logf(pk.rng.next());
                 } else if (a.terminate_on_absorb) {
-                    lc.v[C_ABSORBED_TERM]++;
+                    lc.inc(C_ABSORBED_TERM);
                     flush_run(t, dep_ci, dep_val);
-                    lc.v[C_PACKETS_DONE]++;
+                    lc.inc(C_PACKETS_DONE);
                     again = true;
                 } else {
                     const float u1 = pk.rng.next(), u2 = pk.rng.next();
@@ -493,7 +493,7 @@ __device__ void rg_service(const DevGrid& g, const DevDust& d, const DevSources&
                 if (__shfl_sync(FULL, ab ? 1 : 0, 0)) {
                     if (lane == 0) {
                         vstore(&sh.abort, 1);
-                        lc.v[C_WATCHDOG]++;
+                        lc.inc(C_WATCHDOG);
                     }
                     break;
                 }
@@ -525,8 +525,9 @@ __global__ void __launch_bounds__(256, MINB) k_event_rg(DevGrid g, DevDust d, De
         sh.abort = 0;
     }
     __syncthreads();
+    __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     LocalCounters lc;
-    lc.zero();
+    lc.init(cnt_sh[threadIdx.x >> 5]);
     const int w = threadIdx.x >> 5;
     if (w < RG_WALKERS) rg_walker<G, WAGG>(g, d, o, a, t, st, sh, w, lc);
     else rg_service<G, PEEL>(g, d, s, o, a, t, st, sh, lc);

@@ -70,6 +70,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
+// Untiled bulk copy of `bytes` contiguous bytes (both addresses 16-byte aligned, bytes a
+// multiple of 16) from global to shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    uint64_t gsrc;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(gsrc) : "l"(reinterpret_cast<uint64_t>(src)));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(gsrc), "r"(bytes), "r"(bar)
+        : "memory");
+}
 
 // ---------------------------------------------------------------- proxies and ordering
 // generic-proxy writes to shared memory (st.shared, cp.async) visible to the tensor cores

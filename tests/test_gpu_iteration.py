@@ -245,10 +245,20 @@ def test_event_kernel_reproduces_plain_histories(name):
             rel = np.abs(runs[-1][seen] - acc0[seen]) / acc0[seen]
             assert np.median(rel) < 1e-5
             assert st["n_crossings"] == pytest.approx(sp["n_crossings"], rel=1e-3)
-    # the launch shape and the form of the event kernel (warp-local or regrouped across warps)
-    # never change a history (only the merge order of the deposits)
-    for r in runs[1:]:
+    # the regroup threshold never changes a history (only the merge order of the deposits); nor,
+    # on the Cartesian grid, does the form of the event kernel (warp-local or regrouped across
+    # warps).  On the spherical grid the two forms are compiled at different register budgets (4
+    # and 3 blocks per SM), whose FMA contraction of the walk may differ: there they agree as the
+    # event and plain kernels do
+    for r in runs[1:3]:
         np.testing.assert_allclose(r, runs[0], rtol=1e-6, atol=1e-300)
+    for r in runs[4:6]:
+        np.testing.assert_allclose(r, runs[3], rtol=1e-6, atol=1e-300)
+    if name == "tiny_sphere":
+        np.testing.assert_allclose(runs[3], runs[0], rtol=1e-6, atol=1e-300)
+    else:
+        seen = runs[0] > 0
+        assert np.median(np.abs(runs[3][seen] - runs[0][seen]) / runs[0][seen]) < 1e-5
     # imaging pass: SEDs agree as well
     ref.run_iteration(kernel=hrt.HRT_KERNEL_PLAIN, peel=1, update_temperature=0, n_packets=5000)
     m = hrt.Model(wl)
@@ -263,7 +273,11 @@ def test_event_kernel_reproduces_plain_histories(name):
 @pytest.mark.parametrize("name", ["tiny_sphere", "flared_disk"])
 def test_peel_queue_overflow_is_peeled_inline_with_the_same_result(name):
     # an imaging pass queues its peel-off events for the peel pass; events past the queue's
-    # capacity are walked by the propagation kernel itself: the same rays, the same weights
+    # capacity are walked by the propagation kernel itself: the same rays (equal crossing counts)
+    # and the same weights up to the FP32 rounding of each ray's optical depth (the two kernels
+    # compile the walk separately, and the compiler may fuse its multiply-adds differently: over
+    # n <= a few hundred crossings and tau <= the 40 at which a ray stops, |d tau| stays far
+    # below n * 2^-24 * tau < 1e-3)
     wl = W.WORKLOADS[name](n_packets=100_000)
     if name == "flared_disk":
         wl = W.flared_disk(n_packets=100_000, n_r=80, n_theta=48)
@@ -278,8 +292,9 @@ def test_peel_queue_overflow_is_peeled_inline_with_the_same_result(name):
         runs.append((st, m.sed(), m.image() if wl.img_nx > 0 else None))
     (s0, sed0, img0), (s1, sed1, img1) = runs
     assert s1["n_peel_crossings"] == s0["n_peel_crossings"] and s1["n_crossings"] == s0["n_crossings"]
-    np.testing.assert_allclose(sed1, sed0, rtol=1e-9, atol=1e-300)
+    np.testing.assert_allclose(sed1.sum(axis=1), sed0.sum(axis=1), rtol=1e-6)
+    np.testing.assert_allclose(sed1, sed0, rtol=1e-3, atol=1e-300)
     if img0 is not None:
-        np.testing.assert_allclose(img1, img0, rtol=1e-9, atol=1e-300)
+        np.testing.assert_allclose(img1, img0, rtol=1e-3, atol=1e-300)
     with pytest.raises(hrt.HrtError):
         hrt.Model(wl).run_iteration(peel=1, update_temperature=0, peel_queue_events=-1)
