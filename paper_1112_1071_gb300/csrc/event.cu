@@ -54,6 +54,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
     bool fresh = true;
     float rho_nx = 0.f;
     float3 wn = make_float3(0.f, 0.f, 0.f);
+    const L2Hints l2 = make_l2_hints();
 
     auto start_walk = [&]() {
         if constexpr (MRW) {
@@ -116,12 +117,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
             r[10] = (float)pk.r.i; r[11] = (float)pk.r.j; r[12] = (float)pk.r.k;
             r[13] = pk.nu; r[14] = 0.f; r[15] = (float)where;
         }
-        flush_run(t, dep_ci, dep_val);
+        flush_run<true>(t, dep_ci, dep_val, l2.keep);
         dep_ci = -1;
         mode = M_DONE;
     };
     auto end_packet = [&]() {
-        flush_run(t, dep_ci, dep_val);
+        flush_run<true>(t, dep_ci, dep_val, l2.keep);
         dep_ci = -1;
         dep_val = 0.f;
         lc.inc(C_PACKETS_DONE);
@@ -152,7 +153,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
         if (pk.r.ci == dep_ci) {
             dep_val += v;
         } else {
-            flush_run(t, dep_ci, dep_val);
+            flush_run<true>(t, dep_ci, dep_val, l2.keep);
             dep_ci = pk.r.ci;
             dep_val = v;
         }
@@ -243,7 +244,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                 } else {
                     l = cell_exit<G>(g, pk.r, axis, dir);
                 }
-                const float rho = fresh ? __ldg(g.rhoL + pk.r.ci) : rho_nx;
+                const float rho = fresh ? ld_hint(g.rhoL + pk.r.ci, l2.stream) : rho_nx;
                 fresh = false;
                 const float k = rho * pk.dust.chi;
                 const float dtau = k * l;
@@ -280,7 +281,7 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     if constexpr (G == GRID_CARTESIAN) out = cart_step_w(g, pk.r, wn, l, axis);
                     else out = cell_step<G>(g, pk.r, l, axis, dir);
                     if (out) mode = M_ESCAPED;
-                    else rho_nx = __ldg(g.rhoL + pk.r.ci);      // the next crossing's density, ahead of use
+                    else rho_nx = ld_hint(g.rhoL + pk.r.ci, l2.stream);      // the next crossing's density, ahead of use
                     if constexpr (G != GRID_CARTESIAN) {
                         if (!tiny_step(pk.r, l)) zero_run = 0;
                         else if (++zero_run > ZERO_RUN_LIMIT) { nudge(pk.r); zero_run = 0; }
@@ -294,12 +295,12 @@ __device__ __forceinline__ void event_loop(const DevGrid& g, const DevDust& d, c
                     ray_steps = 0;
                 }
             }
-            flush_deposit<WAGG>(t.acc, t.visits, flushing, fci, fval);
+            flush_deposit<WAGG, true>(t.acc, t.visits, flushing, fci, fval, l2.keep);
             if (((++steps) & 4095u) == 0) watchdog(steps);
         }
         if (((++rounds) & 255u) == 0) watchdog(rounds);
     }
-    flush_run(t, dep_ci, dep_val);
+    flush_run<true>(t, dep_ci, dep_val, l2.keep);
 }
 
 // ---------------------------------------------------------------- one model
@@ -348,10 +349,10 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     ll.block = 256;
     PropagateJob j = job;
     const bool peel = job.args.peel != 0;
-    // default shapes (measured on GB300): Lucy iterations at 3 blocks of 256 per SM (80
-    // registers) on Cartesian grids and 4 (64 registers) on spherical ones, 7 % faster there
-    // despite some spilling (and 0.5 % slower on the 256^3 cloud); imaging passes at 2 (128
-    // registers: with the queue push and the in-place peel-off the kernel spills at 80); warps stay
+    // default shapes (measured on GB300): Lucy iterations at 4 blocks of 256 per SM (64
+    // registers; with the L2 hints 5 % faster than 3 on the 256^3 cloud, 7 % on the disk despite
+    // some spilling there), 3 on cylindrical grids; imaging passes at 3 (80 registers: 6-8 %
+    // faster than 2 on the disk and the cloud); warps stay
     // in the walk phase while at least 24 lanes walk on curvilinear grids, 20 on Cartesian runs of
     // >= 4M packets, 12 for small Cartesian runs whose tail dominates
     int rg_default = DEFAULT_REGROUP;
@@ -359,7 +360,7 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 2 : job.grid.type == GRID_SPHERICAL ? 4 : 3);
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 3 : job.grid.type == GRID_CYLINDRICAL ? 3 : 4);
     cudaError_t e;
     if (job.grid.type == GRID_CARTESIAN)
         e = peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)

@@ -46,19 +46,48 @@ __device__ __forceinline__ bool past_deadline(const RunArgs& a, const Tallies& t
     return false;
 }
 
+// L2 eviction priorities for the walk (per-access cache policies, `createpolicy`): the FP64
+// reductions into the accumulators are marked evict_last and the density loads evict_first, so
+// that where the two arrays together exceed L2 (the 256^3 cloud: 128 + 64 MiB against 126 MB)
+// the accumulator sectors -- whose misses cost a read and a write-back -- are the ones that stay.
+struct L2Hints {
+    uint64_t keep, stream;
+};
+__device__ __forceinline__ L2Hints make_l2_hints() {
+    L2Hints h;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
+    return h;
+}
+__device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(__cvta_generic_to_global(p)), "l"(pol));
+    return v;
+}
+template <bool HINT>
+__device__ __forceinline__ void add_acc(double* a, double v, uint64_t pol) {
+    if constexpr (HINT)
+        asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(a)), "d"(v),
+                     "l"(pol)
+                     : "memory");
+    else
+        atomicAdd(a, v);
+}
+
 // Deposit of one lane: merged while the packet stays in one cell, flushed on a cell change.
 // With WAGG, the flushes of all lanes at one step are grouped by cell (match.any) and each
 // group adds its sum (formed in FP64) with one FP64 atomic.  Each flushed run is one packet entry of the cell,
 // counted into `visits` when the diffusion approximation needs it.
-template <bool WAGG>
-__device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, bool flushing, int32_t ci, float v) {
+template <bool WAGG, bool HINT = false>
+__device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, bool flushing, int32_t ci, float v,
+                                              uint64_t pol = 0) {
     if constexpr (WAGG) {
         const unsigned lane = threadIdx.x & 31u;
         const int key = flushing ? ci : -1 - (int)lane;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         if (!flushing) return;
         if (__popc(peers) == 1) {
-            atomicAdd(acc + ci, widen(v));
+            add_acc<HINT>(acc + ci, widen(v), pol);
             if (visits) atomicAdd(visits + ci, 1u);
             return;
         }
@@ -67,21 +96,22 @@ __device__ __forceinline__ void flush_deposit(double* acc, uint32_t* visits, boo
         double sum = 0.0;
         for (unsigned m = peers; m; m &= m - 1) sum += widen(__shfl_sync(peers, v, __ffs(m) - 1));
         if (lane == (unsigned)(__ffs(peers) - 1)) {
-            atomicAdd(acc + ci, sum);
+            add_acc<HINT>(acc + ci, sum, pol);
             if (visits) atomicAdd(visits + ci, (uint32_t)__popc(peers));
         }
     } else {
         if (flushing) {
-            atomicAdd(acc + ci, widen(v));
+            add_acc<HINT>(acc + ci, widen(v), pol);
             if (visits) atomicAdd(visits + ci, 1u);
         }
     }
 }
 
 // End of a lane's run outside the walk step (packet end, watchdog, kernel end).
-__device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v) {
+template <bool HINT = false>
+__device__ __forceinline__ void flush_run(const Tallies& t, int32_t ci, float v, uint64_t pol = 0) {
     if (ci < 0) return;
-    if (v != 0.f) atomicAdd(t.acc + ci, widen(v));
+    if (v != 0.f) add_acc<HINT>(t.acc + ci, widen(v), pol);
     if (t.visits) atomicAdd(t.visits + ci, 1u);
 }
 

@@ -97,6 +97,27 @@ def bench_conv(torch, log, reps=5):
             row[name + "_ms"] = e0.elapsed_time(e1) / reps
         out.append(row)
         log(json.dumps(row))
+    # one U-Net training step (forward, backward, Adam) at batch 2 x 128^3, the warm start's size
+    widths = (32, 64, 192)
+    wa = (C.c_int * 3)(*widths)
+    net = C.c_void_p()
+    hrt.check(None, L.hrt_net_create_widths(C.byref(net), 0, C.cast(wa, C.c_void_p), 2, 7, None))
+    n, d = 2, 128
+    x = torch.randn((n, d, d, d, 2), device="cuda")
+    t = torch.randn((n, d, d, d), device="cuda")
+    loss = C.c_double()
+    for _ in range(2):
+        hrt.check(None, L.hrt_net_train_step(net, n, d, d, d, x.data_ptr(), t.data_ptr(), 1e-4, C.byref(loss)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        hrt.check(None, L.hrt_net_train_step(net, n, d, d, d, x.data_ptr(), t.data_ptr(), 1e-4, C.byref(loss)))
+    torch.cuda.synchronize()
+    row = dict(shape=f"U-Net {widths} training step, batch {n} x {d}^3",
+               ms=1e3 * (time.perf_counter() - t0) / reps)
+    L.hrt_net_destroy(net)
+    out.append(row)
+    log(json.dumps(row))
     return out
 
 
