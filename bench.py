@@ -62,10 +62,10 @@ B_CROSS = 20.0
 B_PEEL = 4.0
 B_REEMIT = 400.0
 # DRAM bytes (read + write) per crossing of the Lucy propagation kernel on the 256^3 cloud, from
-# an ncu capture of the current k_event (a 1e6-packet Lucy launch on the full grid; DRAM traffic
-# there comes from the cache misses of the walk, so it grows with the crossings): per launch =
-# this x the launch's crossings
-TRAFFIC_PER_CROSSING = 51.9
+# an ncu capture of the current k_event (the third Lucy launch of 5e6 packets on the full grid:
+# 58.3 GB for 9.55e8 crossings; DRAM traffic there comes from the cache misses of the walk, so it
+# grows with the crossings): per launch = this x the launch's crossings
+TRAFFIC_PER_CROSSING = 61.1
 
 
 def parse():

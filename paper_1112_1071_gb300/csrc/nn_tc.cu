@@ -250,26 +250,33 @@ cudaError_t conv3d_phased(const bf16* in, const bf16* Bw, const float* bias, bf1
 // gives up after WAIT_LIMIT_NS (or when another role has given up): the block records the error,
 // lets its own loads and MMAs drain (bounded), frees its tensor memory and returns.
 constexpr int TM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
-constexpr int TM_HX = BRICK_X + 2;                  // halo voxels along x
-constexpr int TM_ROW = TM_HX * 16;                  // one (z, y) row of one channel half: 160 bytes
-constexpr int TM_HALF_BYTES = 3 * HALO_Y * TM_ROW;  // one channel half of the halo (what TMA delivers)
-constexpr int TM_HALF = (TM_HALF_BYTES + 127) & ~127;   // its region, 128-byte aligned
 
-template <int BN>
+// NT = 16 x 8-voxel tiles side by side along x per work item: they share one halo and one fetch
+// of the weights (the weights are most of a stage's bytes)
+template <int BN, int NT>
 struct TmShape {
+    static constexpr int HX = NT * BRICK_X + 2;     // halo voxels along x
+    static constexpr int ROW = HX * 16;             // one (z, y) row of one channel half
+    static constexpr int HALF_BYTES = 3 * HALO_Y * ROW;            // one channel half of the halo
+    static constexpr int HALF = (HALF_BYTES + 127) & ~127;         // its region, 128-byte aligned
     static constexpr int WHALF = 27 * BN * 16;      // one channel half of all taps' weights
-    static constexpr int STAGE = 2 * TM_HALF + 2 * WHALF;
-    static constexpr int TX = 2 * TM_HALF_BYTES + 2 * WHALF;       // bytes a stage's loads deliver
-    static constexpr int STAGES = BN <= 32 ? 4 : 3;                // as many as fit in 227 KB
+    static constexpr int STAGE = 2 * HALF + 2 * WHALF;
+    static constexpr int TX = 2 * HALF_BYTES + 2 * WHALF;          // bytes a stage's loads deliver
+    static constexpr int FIT = (227 * 1024 - 1024 - 128) / STAGE;  // stages that fit in 227 KB
+    static constexpr int STAGES = FIT > 4 ? 4 : FIT;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 128;       // + alignment slack, barriers
+    static constexpr uint32_t NCOLS = 2 * NT * BN;  // two accumulators of NT tiles each
+    static_assert(STAGES >= 2, "two stages at least");
+    static_assert(NCOLS == 64 || NCOLS == 128 || NCOLS == 256, "tensor memory columns: a power of two");
 };
 
-template <int BN>
+template <int BN, int NT>
 __global__ void __launch_bounds__(TM_THREADS, 1)
     k_conv3d_tma(const __grid_constant__ CUtensorMap act, const bf16* __restrict__ Bp, const float* __restrict__ bias, bf16* __restrict__ out, int N, int D, int H, int W, int Cin, int Cout,
                  int flip, int relu) {
-    constexpr int STAGE = TmShape<BN>::STAGE, WHALF = TmShape<BN>::WHALF, TM_STAGES = TmShape<BN>::STAGES;
-    constexpr uint32_t NCOLS = 2 * BN;
+    using S = TmShape<BN, NT>;
+    constexpr int STAGE = S::STAGE, WHALF = S::WHALF, TM_STAGES = S::STAGES, TM_HALF = S::HALF, TM_ROW = S::ROW;
+    constexpr uint32_t NCOLS = S::NCOLS;
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, BN);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = tc::smem_addr(smem_raw);
@@ -329,13 +336,13 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         }
     };
 
-    const int nbx = (W + BRICK_X - 1) / BRICK_X, nby = (H + BRICK_Y - 1) / BRICK_Y, ntn = Cout / BN;
+    const int nbx = (W + NT * BRICK_X - 1) / (NT * BRICK_X), nby = (H + BRICK_Y - 1) / BRICK_Y, ntn = Cout / BN;
     const long long ntiles = (long long)N * D * nby * nbx * ntn;
     const int kchunks = Cin / KC;
     auto decode = [&](long long t, int& b, int& z, int& y0, int& x0, int& n0) {
         n0 = (int)(t % ntn) * BN;
         t /= ntn;
-        x0 = (int)(t % nbx) * BRICK_X;
+        x0 = (int)(t % nbx) * (NT * BRICK_X);
         t /= nbx;
         y0 = (int)(t % nby) * BRICK_Y;
         t /= nby;
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
                         break;
                     }
                     const uint32_t sb = base + st * STAGE;
-                    tc::mbar_arrive_expect_tx(full(st), (uint32_t)TmShape<BN>::TX);
+                    tc::mbar_arrive_expect_tx(full(st), (uint32_t)S::TX);
                     for (int h = 0; h < 2; ++h)
                         tc::tma_load_5d(sb + h * TM_HALF, &act, c * KC + h * 8, x0 - 1, y0 - 1, z - 1, b, full(st));
                     for (int h = 0; h < 2; ++h)
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
                 const int buf = j & 1;
                 if (!wait(acce(buf), (((uint32_t)j >> 1) & 1u) ^ 1u)) break;
                 tc::fence_after_sync();
-                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                const uint32_t acc = tmem + (uint32_t)(buf * NT * BN);
                 for (int c = 0; c < kchunks; ++c, ++it) {
                     const int st = (int)(it % TM_STAGES);
                     if (!wait(full(st), (uint32_t)((it / TM_STAGES) & 1))) {
@@ -398,9 +405,13 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 #pragma unroll
                     for (int tap = 0; tap < 27; ++tap) {
                         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                        const uint32_t aoff = ((dz * HALO_Y + dy) * TM_ROW + dx * 16) >> 4;
                         const uint32_t boff = (flip ? (26 - tap) * BN : tap * BN);   // x 16 bytes >> 4
-                        tc::mma_bf16(acc, a0 + aoff, b0 + boff, IDESC, (c > 0 || tap > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int u = 0; u < NT; ++u) {
+                            const uint32_t aoff = ((dz * HALO_Y + dy) * TM_ROW + (u * BRICK_X + dx) * 16) >> 4;
+                            tc::mma_bf16(acc + (uint32_t)(u * BN), a0 + aoff, b0 + boff, IDESC,
+                                         (c > 0 || tap > 0) ? 1u : 0u);
+                        }
                     }
                     tc::mma_commit(empty(st));          // the stage is free once these MMAs complete
                 }
@@ -422,31 +433,34 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             tc::fence_after_sync();
             int b, z, y0, x0, n0;
             decode(t, b, z, y0, x0, n0);
-            const int yy = y0 + tid / BRICK_X, xx = x0 + tid % BRICK_X;
-            const bool vin = yy < H && xx < W;
             bf16* outb = out + (long long)b * V * Cout;
-            const long long v = ((long long)z * H + yy) * W + xx;
-            const uint32_t row_addr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float accv[16];
-                tc::tmem_ld16(row_addr + (uint32_t)c0, accv);
-                if (vin) {
-                    __align__(16) __nv_bfloat162 o[8];
+            for (int u = 0; u < NT; ++u) {
+                const int yy = y0 + tid / BRICK_X, xx = x0 + u * BRICK_X + tid % BRICK_X;
+                const bool vin = yy < H && xx < W;
+                const long long v = ((long long)z * H + yy) * W + xx;
+                const uint32_t row_addr = tmem + (uint32_t)((buf * NT + u) * BN) + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    float accv[16];
+                    tc::tmem_ld16(row_addr + (uint32_t)c0, accv);
+                    if (vin) {
+                        __align__(16) __nv_bfloat162 o[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int n = n0 + c0 + 2 * i;
-                        float a0 = accv[2 * i] + (bias ? bias[n] : 0.f);
-                        float a1 = accv[2 * i + 1] + (bias ? bias[n + 1] : 0.f);
-                        if (relu) {
-                            a0 = fmaxf(a0, 0.f);
-                            a1 = fmaxf(a1, 0.f);
+                        for (int i = 0; i < 8; ++i) {
+                            const int n = n0 + c0 + 2 * i;
+                            float a0 = accv[2 * i] + (bias ? bias[n] : 0.f);
+                            float a1 = accv[2 * i + 1] + (bias ? bias[n + 1] : 0.f);
+                            if (relu) {
+                                a0 = fmaxf(a0, 0.f);
+                                a1 = fmaxf(a1, 0.f);
+                            }
+                            o[i] = __floats2bfloat162_rn(a0, a1);
                         }
-                        o[i] = __floats2bfloat162_rn(a0, a1);
+                        uint4* dst = reinterpret_cast<uint4*>(outb + v * Cout + n0 + c0);
+                        dst[0] = *reinterpret_cast<const uint4*>(&o[0]);
+                        dst[1] = *reinterpret_cast<const uint4*>(&o[4]);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(outb + v * Cout + n0 + c0);
-                    dst[0] = *reinterpret_cast<const uint4*>(&o[0]);
-                    dst[1] = *reinterpret_cast<const uint4*>(&o[4]);
                 }
             }
             tc::fence_before_sync();
@@ -479,30 +493,32 @@ EncodeTiled encode_tiled() {
 }
 }  // namespace
 
-template <int BN>
+template <int BN, int NT>
 static cudaError_t launch_tma(const bf16* in, const bf16* Bp, const float* bias, bf16* out, int N, int D, int H, int W,
                               int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
+    using S = TmShape<BN, NT>;
     EncodeTiled enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap act;
     const cuuint64_t adim[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
     const cuuint64_t astr[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
                                 (cuuint64_t)D * H * W * Cin * 2};
-    const cuuint32_t abox[5] = {8, TM_HX, HALO_Y, 3, 1};
+    const cuuint32_t abox[5] = {8, (cuuint32_t)S::HX, HALO_Y, 3, 1};
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), adim, astr, abox, ones,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    constexpr int SMEM = TmShape<BN>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    constexpr int SMEM = S::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tma<BN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const long long ntiles = (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + BRICK_X - 1) / BRICK_X) * (Cout / BN);
+    const long long ntiles =
+        (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + NT * BRICK_X - 1) / (NT * BRICK_X)) * (Cout / BN);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_conv3d_tma<BN><<<grid, TM_THREADS, SMEM, s>>>(act, Bp, bias, out, N, D, H, W, Cin, Cout, flip ? 1 : 0,
+    k_conv3d_tma<BN, NT><<<grid, TM_THREADS, SMEM, s>>>(act, Bp, bias, out, N, D, H, W, Cin, Cout, flip ? 1 : 0,
                                                     relu ? 1 : 0);
     return cudaGetLastError();
 }
@@ -513,8 +529,12 @@ cudaError_t conv3d(const bf16* in, const bf16* Bw, const bf16* Bp, const float* 
                    int W, int Cin, int Cout, bool flip, bool relu, cudaStream_t s) {
     if (Cin % 16 != 0 || Cout % 32 != 0 || Cin <= 0 || Cout <= 0) return cudaErrorInvalidValue;
     if (Bp && encode_tiled()) {
-        if (tma_tile_n(Cout) == 64) return launch_tma<64>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
-        return launch_tma<32>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+        const bool two = W > BRICK_X;       // two tiles per weight fetch unless the grid is one tile wide
+        if (tma_tile_n(Cout) == 64)
+            return two ? launch_tma<64, 2>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s)
+                       : launch_tma<64, 1>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
+        return two ? launch_tma<32, 2>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s)
+                   : launch_tma<32, 1>(in, Bp, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
     }
     return conv3d_phased(in, Bw, bias, out, N, D, H, W, Cin, Cout, flip, relu, s);
 }
