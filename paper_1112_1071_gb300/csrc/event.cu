@@ -421,14 +421,15 @@ static void launch_batch_shape(const BatchModel* models, const BatchChunk* chunk
                                                                                  state, regroup);
 }
 
-// Default shape: 3 blocks of 256 per SM, regroup 20; the autotuner times others (2-4 blocks).
+// Default shape as for one model's Lucy iteration: 4 blocks of 256 per SM, regroup 20; the
+// autotuner times others (2-4 blocks).
 cudaError_t launch_propagate_batch(int gtype, const BatchModel* models, const BatchChunk* chunks, int nchunks,
                                    unsigned* chunk_counter, const BatchState* state, const Launch& l, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : 20;
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 3;
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : 4;
     if (gtype == GRID_CARTESIAN) {
         if (bps >= 4) launch_batch_shape<GRID_CARTESIAN, 4>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);
         else if (bps == 3) launch_batch_shape<GRID_CARTESIAN, 3>(models, chunks, nchunks, chunk_counter, state, bps, regroup, sms, s);

@@ -349,74 +349,120 @@ cudaError_t bias_grad(const bf16* dy, float* db, long long V, int C, cudaStream_
     return cudaGetLastError();
 }
 
-__global__ void k_relu_mask(bf16* __restrict__ g, const bf16* __restrict__ h, long long n) {
-    GRID_STRIDE(i, n) {
-        if (!(__bfloat162float(h[i]) > 0.f)) g[i] = __float2bfloat16(0.f);
+// Channels-last tensors with C % 8 == 0: each thread moves 8 channels (16 bytes) of one voxel.
+__device__ __forceinline__ void unpack8(const uint4& u, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float* f) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    return u;
+}
+__device__ __forceinline__ uint4 ld8(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st8(bf16* p, const uint4& u) { *reinterpret_cast<uint4*>(p) = u; }
+
+__global__ void k_relu_mask(bf16* __restrict__ g, const bf16* __restrict__ h, long long n8) {
+    GRID_STRIDE(i, n8) {
+        float gv[8], hv[8];
+        unpack8(ld8(g + 8 * i), gv);
+        unpack8(ld8(h + 8 * i), hv);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (!(hv[k] > 0.f)) gv[k] = 0.f;
+        st8(g + 8 * i, pack8(gv));
     }
 }
 
 cudaError_t relu_mask(bf16* g, const bf16* h, long long n, cudaStream_t s) {
-    k_relu_mask<<<blocks_for(n), 256, 0, s>>>(g, h, n);
+    if (n % 8) return cudaErrorInvalidValue;
+    k_relu_mask<<<blocks_for(n / 8), 256, 0, s>>>(g, h, n / 8);
     return cudaGetLastError();
 }
 
+// 2x2x2 average pooling: one thread per (output voxel, 8 channels)
 __global__ void k_pool2(const bf16* __restrict__ x, bf16* __restrict__ y, int N, int D, int H, int W, int C) {
-    const int d = D / 2, h = H / 2, w = W / 2;
-    const long long n = (long long)N * d * h * w * C;
+    const int d = D / 2, h = H / 2, w = W / 2, C8 = C / 8;
+    const long long n = (long long)N * d * h * w * C8;
     GRID_STRIDE(i, n) {
-        const int c = (int)(i % C);
-        long long r = i / C;
+        const int c = (int)(i % C8) * 8;
+        long long r = i / C8;
         const int xx = (int)(r % w); r /= w;
         const int yy = (int)(r % h); r /= h;
         const int zz = (int)(r % d);
         const long long nb = r / d;
-        float s = 0.f;
+        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
-                for (int e = 0; e < 2; ++e)
-                    s += __bfloat162float(x[(((nb * D + 2 * zz + a) * H + 2 * yy + b) * W + 2 * xx + e) * C + c]);
-        y[i] = __float2bfloat16(0.125f * s);
+                for (int e = 0; e < 2; ++e) {
+                    float v[8];
+                    unpack8(ld8(x + (((nb * D + 2 * zz + a) * H + 2 * yy + b) * W + 2 * xx + e) * C + c), v);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) s8[k] += v[k];
+                }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s8[k] *= 0.125f;
+        st8(y + i * 8, pack8(s8));
     }
 }
 
 __global__ void k_pool2_back(const bf16* __restrict__ dy, bf16* __restrict__ dx, int N, int D, int H, int W, int C,
                              int accumulate) {
-    const long long n = (long long)N * D * H * W * C;
+    const int C8 = C / 8;
+    const long long n = (long long)N * D * H * W * C8;
     GRID_STRIDE(i, n) {
-        const int c = (int)(i % C);
-        long long r = i / C;
+        const int c = (int)(i % C8) * 8;
+        long long r = i / C8;
         const int xx = (int)(r % W); r /= W;
         const int yy = (int)(r % H); r /= H;
         const int zz = (int)(r % D);
         const long long nb = r / D;
-        const float g = 0.125f * __bfloat162float(dy[(((nb * (D / 2) + zz / 2) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c]);
-        dx[i] = __float2bfloat16(accumulate ? g + __bfloat162float(dx[i]) : g);
+        float g[8];
+        unpack8(ld8(dy + (((nb * (D / 2) + zz / 2) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c), g);
+        if (accumulate) {
+            float o[8];
+            unpack8(ld8(dx + i * 8), o);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) g[k] = 0.125f * g[k] + o[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) g[k] *= 0.125f;
+        }
+        st8(dx + i * 8, pack8(g));
     }
 }
 
 // nearest 2x upsampling of x [N][D/2][H/2][W/2][C1] into channels [0, C1) of y [N][D][H][W][Ctot]
 __global__ void k_up2_into(const bf16* __restrict__ x, bf16* __restrict__ y, int N, int D, int H, int W, int C1,
                            int Ctot) {
-    const long long n = (long long)N * D * H * W * C1;
+    const int C8 = C1 / 8;
+    const long long n = (long long)N * D * H * W * C8;
     GRID_STRIDE(i, n) {
-        const int c = (int)(i % C1);
-        long long r = i / C1;
+        const int c = (int)(i % C8) * 8;
+        long long r = i / C8;
         const int xx = (int)(r % W); r /= W;
         const int yy = (int)(r % H); r /= H;
         const int zz = (int)(r % D);
         const long long nb = r / D;
-        y[(((nb * D + zz) * H + yy) * W + xx) * Ctot + c] =
-            x[(((nb * (D / 2) + zz / 2) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C1 + c];
+        st8(y + (((nb * D + zz) * H + yy) * W + xx) * Ctot + c,
+            ld8(x + (((nb * (D / 2) + zz / 2) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C1 + c));
     }
 }
 
 // copy s [N*V][C2] into channels [off, off + C2) of y [N*V][Ctot]
 __global__ void k_copy_into(const bf16* __restrict__ s, bf16* __restrict__ y, long long NV, int C2, int off, int Ctot) {
-    const long long n = NV * C2;
-    GRID_STRIDE(i, n) {
-        const long long v = i / C2;
-        const int c = (int)(i % C2);
-        y[v * Ctot + off + c] = s[i];
+    const int C8 = C2 / 8;
+    GRID_STRIDE(i, NV * C8) {
+        const long long v = i / C8;
+        const int c = (int)(i % C8) * 8;
+        st8(y + v * Ctot + off + c, ld8(s + i * 8));
     }
 }
 
@@ -424,50 +470,63 @@ __global__ void k_copy_into(const bf16* __restrict__ s, bf16* __restrict__ y, lo
 // gradient), channels [C1, Ctot) added into dskip
 __global__ void k_concat_back(const bf16* __restrict__ g, bf16* __restrict__ dx, bf16* __restrict__ dskip, int N, int D,
                               int H, int W, int C1, int Ctot) {
-    const int d = D / 2, h = H / 2, w = W / 2;
-    const long long n1 = (long long)N * d * h * w * C1;
+    const int d = D / 2, h = H / 2, w = W / 2, C18 = C1 / 8;
+    const long long n1 = (long long)N * d * h * w * C18;
     GRID_STRIDE(i, n1) {
-        const int c = (int)(i % C1);
-        long long r = i / C1;
+        const int c = (int)(i % C18) * 8;
+        long long r = i / C18;
         const int xx = (int)(r % w); r /= w;
         const int yy = (int)(r % h); r /= h;
         const int zz = (int)(r % d);
         const long long nb = r / d;
-        float s = 0.f;
+        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
-                for (int e = 0; e < 2; ++e)
-                    s += __bfloat162float(g[(((nb * D + 2 * zz + a) * H + 2 * yy + b) * W + 2 * xx + e) * Ctot + c]);
-        dx[i] = __float2bfloat16(s);
+                for (int e = 0; e < 2; ++e) {
+                    float v[8];
+                    unpack8(ld8(g + (((nb * D + 2 * zz + a) * H + 2 * yy + b) * W + 2 * xx + e) * Ctot + c), v);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) s8[k] += v[k];
+                }
+        st8(dx + i * 8, pack8(s8));
     }
-    const int C2 = Ctot - C1;
-    const long long n2 = (long long)N * D * H * W * C2;
+    const int C28 = (Ctot - C1) / 8;
+    const long long n2 = (long long)N * D * H * W * C28;
     GRID_STRIDE(j, n2) {
-        const long long v = j / C2;
-        const int c = (int)(j % C2);
-        dskip[j] = __float2bfloat16(__bfloat162float(dskip[j]) + __bfloat162float(g[v * Ctot + C1 + c]));
+        const long long v = j / C28;
+        const int c = (int)(j % C28) * 8;
+        float a8[8], b8[8];
+        unpack8(ld8(dskip + j * 8), a8);
+        unpack8(ld8(g + v * Ctot + C1 + c), b8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a8[k] += b8[k];
+        st8(dskip + j * 8, pack8(a8));
     }
 }
 
 cudaError_t pool2(const bf16* x, bf16* y, int N, int D, int H, int W, int C, cudaStream_t s) {
-    k_pool2<<<blocks_for((long long)N * D * H * W * C / 8), 256, 0, s>>>(x, y, N, D, H, W, C);
+    if (C % 8) return cudaErrorInvalidValue;
+    k_pool2<<<blocks_for((long long)N * D * H * W * C / 64), 256, 0, s>>>(x, y, N, D, H, W, C);
     return cudaGetLastError();
 }
 cudaError_t pool2_back(const bf16* dy, bf16* dx, int N, int D, int H, int W, int C, bool accumulate, cudaStream_t s) {
-    k_pool2_back<<<blocks_for((long long)N * D * H * W * C), 256, 0, s>>>(dy, dx, N, D, H, W, C, accumulate);
+    if (C % 8) return cudaErrorInvalidValue;
+    k_pool2_back<<<blocks_for((long long)N * D * H * W * C / 8), 256, 0, s>>>(dy, dx, N, D, H, W, C, accumulate);
     return cudaGetLastError();
 }
 cudaError_t concat_up(const bf16* low, const bf16* skip, bf16* y, int N, int D, int H, int W, int C1, int C2,
                       cudaStream_t s) {
-    k_up2_into<<<blocks_for((long long)N * D * H * W * C1), 256, 0, s>>>(low, y, N, D, H, W, C1, C1 + C2);
-    k_copy_into<<<blocks_for((long long)N * D * H * W * C2), 256, 0, s>>>(skip, y, (long long)N * D * H * W, C2, C1,
-                                                                        C1 + C2);
+    if (C1 % 8 || C2 % 8) return cudaErrorInvalidValue;
+    k_up2_into<<<blocks_for((long long)N * D * H * W * C1 / 8), 256, 0, s>>>(low, y, N, D, H, W, C1, C1 + C2);
+    k_copy_into<<<blocks_for((long long)N * D * H * W * C2 / 8), 256, 0, s>>>(skip, y, (long long)N * D * H * W, C2,
+                                                                            C1, C1 + C2);
     return cudaGetLastError();
 }
 cudaError_t concat_up_back(const bf16* g, bf16* dlow, bf16* dskip, int N, int D, int H, int W, int C1, int C2,
                            cudaStream_t s) {
-    k_concat_back<<<blocks_for((long long)N * D * H * W * (C1 + C2)), 256, 0, s>>>(g, dlow, dskip, N, D, H, W, C1,
-                                                                                  C1 + C2);
+    if (C1 % 8 || C2 % 8) return cudaErrorInvalidValue;
+    k_concat_back<<<blocks_for((long long)N * D * H * W * (C1 + C2) / 8), 256, 0, s>>>(g, dlow, dskip, N, D, H, W, C1,
+                                                                                      C1 + C2);
     return cudaGetLastError();
 }
 
@@ -476,7 +535,12 @@ __global__ void k_head(const bf16* __restrict__ h, const float* __restrict__ w, 
                        float* __restrict__ y, long long NV, int C) {
     GRID_STRIDE(v, NV) {
         float s = b[0];
-        for (int c = 0; c < C; ++c) s += __bfloat162float(h[v * C + c]) * w[c];
+        for (int c = 0; c < C; c += 8) {
+            float hv[8];
+            unpack8(ld8(h + v * C + c), hv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s += hv[k] * w[c + k];
+        }
         y[v] = s;
     }
 }
@@ -493,19 +557,35 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ t,
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, part / (double)NV);
 }
 
-// head backward: dh[v][c] = dy[v] w[c]; dw[c] += sum_v h[v][c] dy[v]; db += sum_v dy[v]
+// head backward: dh[v][c] = dy[v] w[c]; dw[c] += sum_v h[v][c] dy[v]; db += sum_v dy[v].  A thread
+// keeps one group of 8 channels and strides over voxels, summing its share of dw (and db) in
+// registers; the block adds the threads' sums in shared memory, then one atomic per channel.
 __global__ void k_head_back(const bf16* __restrict__ h, const float* __restrict__ w, const float* __restrict__ dy,
                             bf16* __restrict__ dh, float* __restrict__ dw, float* __restrict__ db, long long NV, int C) {
     extern __shared__ float sacc[];   // [C + 1]
     for (int c = threadIdx.x; c <= C; c += blockDim.x) sacc[c] = 0.f;
     __syncthreads();
-    GRID_STRIDE(v, NV) {
-        const float g = dy[v];
-        for (int c = 0; c < C; ++c) {
-            dh[v * C + c] = __float2bfloat16(g * w[c]);
-            atomicAdd(&sacc[c], __bfloat162float(h[v * C + c]) * g);
+    const int C8 = C / 8, per = (int)blockDim.x / C8;        // voxels a block takes per round
+    const int cg = (int)threadIdx.x % C8, row = (int)threadIdx.x / C8;
+    if (row < per) {
+        float wv[8], acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, accb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) wv[k] = w[cg * 8 + k];
+        for (long long v = (long long)blockIdx.x * per + row; v < NV; v += (long long)gridDim.x * per) {
+            const float g = dy[v];
+            float hv[8], o[8];
+            unpack8(ld8(h + v * C + cg * 8), hv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                o[k] = g * wv[k];
+                acc[k] += hv[k] * g;
+            }
+            st8(dh + v * C + cg * 8, pack8(o));
+            accb += g;
         }
-        atomicAdd(&sacc[C], g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(&sacc[cg * 8 + k], acc[k]);
+        if (cg == 0) atomicAdd(&sacc[C], accb);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(dw + c, sacc[c]);
@@ -513,6 +593,7 @@ __global__ void k_head_back(const bf16* __restrict__ h, const float* __restrict_
 }
 
 cudaError_t head_forward(const bf16* h, const float* w, const float* b, float* y, long long NV, int C, cudaStream_t s) {
+    if (C % 8) return cudaErrorInvalidValue;
     k_head<<<blocks_for(NV), 256, 0, s>>>(h, w, b, y, NV, C);
     return cudaGetLastError();
 }
@@ -522,7 +603,8 @@ cudaError_t mse_loss(const float* y, const float* t, float* dy, double* loss, lo
 }
 cudaError_t head_backward(const bf16* h, const float* w, const float* dy, bf16* dh, float* dw, float* db, long long NV,
                           int C, cudaStream_t s) {
-    unsigned g = blocks_for(NV);
+    if (C % 8 || C / 8 > 256) return cudaErrorInvalidValue;
+    unsigned g = blocks_for(NV * (C / 8));
     if (g > 1024) g = 1024;
     k_head_back<<<g, 256, sizeof(float) * (C + 1), s>>>(h, w, dy, dh, dw, db, NV, C);
     return cudaGetLastError();

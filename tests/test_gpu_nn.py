@@ -81,8 +81,11 @@ def test_conv3d_backward_matches_oracle(cin, cout):
 # Sizes that span several 16 x 8-voxel bricks per plane and a ragged tail in x and y, so that
 # interior halos between bricks, many blocks per plane and (weight gradient) the split of the
 # voxels over many blocks with FP32 atomics are all exercised; the last three have more output
-# tiles than the GPU has SMs, so persistent blocks run several tiles each.
-MULTI_BRICK = [((1, 4, 18, 34), 32, 32), ((2, 8, 32, 32), 64, 32), ((2, 8, 32, 32), 16, 32),
+# tiles than the GPU has SMs, so persistent blocks run several tiles each.  The first two: a grid
+# one tile wide (W <= 8: one tile per work item) and W = 17 (the last pair of tiles holds one
+# column).
+MULTI_BRICK = [((2, 5, 7, 6), 32, 64), ((1, 4, 16, 17), 32, 32),
+               ((1, 4, 18, 34), 32, 32), ((2, 8, 32, 32), 64, 32), ((2, 8, 32, 32), 16, 32),
                ((1, 6, 20, 36), 32, 128), ((2, 8, 32, 64), 32, 64), ((1, 6, 20, 36), 64, 192),
                ((3, 9, 33, 41), 16, 32)]
 
