@@ -717,8 +717,263 @@ static cudaError_t launch_wgrad_tc(const bf16* in, const bf16* dy, float* dw, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- weight gradient, brick form
+// dW[tap][i][o] = sum_v in[v + off(tap)][i] dY[v][o] summed brick by brick (16 x 8 voxels of one
+// z-plane).  A CTA owns one dz plane of taps (9 taps), NB input channels and up to 128 output
+// channels, and a range of bricks.  Per brick TMA lands the dY brick (the MMA's A: M = 128 rows of
+// output channels -- rows past the real ones read zeroed regions --, K = 128 voxels, MN-major: a
+// core matrix is 8 voxels x 8 channels) and the input's halo plane z + dz - 1 (B: N = NB input
+// channels; a tap's (dy, dx) shift is only a start offset into the 18 x 10-voxel plane, so the
+// halo is loaded once for its 9 taps).  One thread issues 9 taps x 8 K-steps of tcgen05.mma into
+// nine tensor-memory accumulators that run over all the CTA's bricks; at the end four warps add
+// them into dW with FP32 atomics.  Waits are bounded as in k_conv3d_tma.
+constexpr int WH_THREADS = 192;                           // warps 0-3 epilogue, 4 TMA, 5 MMA
+constexpr int WH_ROW = (BRICK_X + 2) * 16;                // one halo row of 8 channels: 160 bytes
+constexpr int WH_HBYTES = HALO_Y * WH_ROW;                // one 8-channel halo plane: 2880 bytes
+constexpr int WH_HREG = (WH_HBYTES + 127) & ~127;         // its region, 128-byte aligned
+constexpr int WH_DREG = BRICK_X * BRICK_Y * 16;           // one 8-channel dY brick: 2048 bytes
+constexpr int WH_DY = 16 * WH_DREG;                       // 128 output-channel rows: 32 KB
+
+template <int NB>
+struct WhShape {
+    static constexpr int HALO = (NB / 8) * WH_HREG;
+    static constexpr int HALO_AL = (HALO + 1023) & ~1023;
+    static constexpr int STAGE = HALO_AL + WH_DY;
+    static constexpr int STAGES = 4;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 128;
+    static constexpr uint32_t NCOLS = 9 * NB <= 256 ? 256 : 512;
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+template <int NB>
+__global__ void __launch_bounds__(WH_THREADS, 1)
+    k_conv3d_wgrad_tma(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap dym,
+                       float* __restrict__ dw, int N, int D, int H, int W, int Cin, int Cout, int nci, int nco,
+                       int nsplit) {
+    using S = WhShape<NB>;
+    constexpr int STAGE = S::STAGE, WS = S::STAGES;
+    constexpr uint32_t NCOLS = S::NCOLS;
+    // FP32 D, BF16 A and B, both MN-major (bits 15 and 16), M = 128, N = NB
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NB) | (1u << 15) | (1u << 16);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = tc::smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sbar = base + WS * STAGE;
+    unsigned char* const gbar = smem_raw + (sbar - raw);
+    auto full = [&](int st) { return sbar + 8u * st; };
+    auto empty = [&](int st) { return sbar + 8u * (WS + st); };
+    const uint32_t accf = sbar + 8u * (2 * WS);
+    const uint32_t drain = sbar + 8u * (2 * WS + 1);
+    const uint32_t slot = sbar + 8u * (2 * WS + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 8 * (2 * WS + 2) + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // this CTA: (dz, input-channel block, output-channel block, split)
+    int c = blockIdx.x;
+    const int split = c % nsplit;
+    c /= nsplit;
+    const int cob = c % nco;
+    c /= nco;
+    const int cib = c % nci;
+    const int dz = c / nci;
+    const int ci0 = cib * NB, co0 = cob * 128;
+    const int mreal = min(128, Cout - co0);           // output-channel rows that are real
+    const int nbx = (W + BRICK_X - 1) / BRICK_X, nby = (H + BRICK_Y - 1) / BRICK_Y;
+    const long long nbricks = (long long)N * D * nby * nbx;
+    const long long b0 = nbricks * split / nsplit, b1 = nbricks * (split + 1) / nsplit;
+
+    if (tid == 0) {
+        for (int st = 0; st < WS; ++st) {
+            tc::mbar_init(full(st), 1);
+            tc::mbar_init(empty(st), 1);
+        }
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    // the dY regions of rows past mreal stay zero in every stage
+    for (int st = 0; st < WS; ++st) {
+        const int zb = (mreal / 8) * WH_DREG;
+        uint4* z = reinterpret_cast<uint4*>(smem_raw + (base - raw) + st * STAGE + S::HALO_AL + zb);
+        for (int q = tid; q < (WH_DY - zb) / 16; q += WH_THREADS) z[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_proxy_async_smem();
+    if (warp == 0) {
+        tc::tmem_alloc(slot, NCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot) : "memory");
+
+    auto wait = [&](uint32_t bar, uint32_t parity, bool drain_wait = false) -> bool {
+        const uint64_t t0 = tc::global_ns();
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity)
+                : "memory");
+            if (done) return true;
+            if ((*abort_flag && !drain_wait) || tc::global_ns() - t0 > WAIT_LIMIT_NS) {
+                *abort_flag = 1;
+                atomicExch(&g_tc_error, 1);
+                return false;
+            }
+        }
+    };
+    auto decode = [&](long long t, int& b, int& z, int& y0, int& x0) {
+        x0 = (int)(t % nbx) * BRICK_X;
+        t /= nbx;
+        y0 = (int)(t % nby) * BRICK_Y;
+        t /= nby;
+        z = (int)(t % D);
+        b = (int)(t / D);
+    };
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            tc::tma_prefetch_map(&act);
+            tc::tma_prefetch_map(&dym);
+            const uint32_t tx = (uint32_t)((NB / 8) * WH_HBYTES + (mreal / 8) * WH_DREG);
+            long long it = 0;
+            for (long long t = b0; t < b1; ++t, ++it) {
+                const int st = (int)(it % WS);
+                if (!wait(empty(st), ((uint32_t)(it / WS) & 1u) ^ 1u)) break;
+                int b, z, y0, x0;
+                decode(t, b, z, y0, x0);
+                const uint32_t sb = base + st * STAGE;
+                tc::mbar_arrive_expect_tx(full(st), tx);
+                for (int g = 0; g < NB / 8; ++g)
+                    tc::tma_load_5d(sb + g * WH_HREG, &act, ci0 + 8 * g, x0 - 1, y0 - 1, z + dz - 1, b, full(st));
+                for (int g = 0; g < mreal / 8; ++g)
+                    tc::tma_load_5d(sb + S::HALO_AL + g * WH_DREG, &dym, co0 + 8 * g, x0, y0, z, b, full(st));
+            }
+            // no copy may still be landing when the block leaves
+            for (long long k = it - WS; k < it; ++k)
+                if (k >= 0) wait(full((int)(k % WS)), (uint32_t)((k / WS) & 1), true);
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            long long it = 0;
+            bool ok = true;
+            for (long long t = b0; t < b1; ++t, ++it) {
+                const int st = (int)(it % WS);
+                if (!wait(full(st), (uint32_t)((it / WS) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t sb = base + st * STAGE;
+                // A: 8-voxel core matrices 128 B apart along K, 8-channel regions along M;
+                // B: the tap's view of the halo plane, 8-voxel rows 160 B apart along K
+                const uint64_t a0 = tc::smem_desc(sb + S::HALO_AL, 128, WH_DREG);
+                const uint64_t h0 = tc::smem_desc(sb, WH_ROW, WH_HREG);
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t aoff = (kk * 256) >> 4;
+                        const uint32_t boff = (((2 * kk + dy) * (BRICK_X + 2) + dx) * 16) >> 4;
+                        tc::mma_bf16(tmem + (uint32_t)(tap * NB), a0 + aoff, h0 + boff, IDESC,
+                                     (t > b0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(empty(st));
+            }
+            if (ok && b1 > b0) tc::mma_commit(accf);
+            else if (ok) tc::mbar_arrive(accf);
+            tc::mma_commit(drain);
+            wait(drain, 0u, true);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 0-3)
+        bool got = true;
+        if (lane == 0) got = wait(accf, 0u);
+        got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (got && b1 > b0) {
+            tc::fence_after_sync();
+            const int co = co0 + warp * 32 + lane;
+            const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int tp = dz * 9 + tap;
+#pragma unroll 1
+                for (int c0 = 0; c0 < NB; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(row + (uint32_t)(tap * NB + c0), v);
+                    if (warp * 32 + lane < mreal) {
+                        float* dst = dw + ((long long)tp * Cin + ci0 + c0) * Cout + co;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) atomicAdd(dst + (long long)q * Cout, v[q]);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+template <int NB>
+static cudaError_t launch_wgrad_tma(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin,
+                                    int Cout, cudaStream_t s) {
+    using S = WhShape<NB>;
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap act, dym;
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t adim[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t astr[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
+                                (cuuint64_t)D * H * W * Cin * 2};
+    const cuuint32_t abox[5] = {8, BRICK_X + 2, HALO_Y, 1, 1};
+    if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), adim, astr, abox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const cuuint64_t ddim[5] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t dstr[4] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2,
+                                (cuuint64_t)D * H * W * Cout * 2};
+    const cuuint32_t dbox[5] = {8, BRICK_X, BRICK_Y, 1, 1};
+    if (enc(&dym, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(dy), ddim, dstr, dbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_tma<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int nci = Cin / NB, nco = (Cout + 127) / 128;
+    const long long nbricks = (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + BRICK_X - 1) / BRICK_X);
+    const int cols = 3 * nci * nco;
+    // one wave of one CTA per SM, at least 4 bricks per CTA
+    long long nsplit = sms / cols;
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > nbricks / 4) nsplit = nbricks / 4 > 0 ? nbricks / 4 : 1;
+    k_conv3d_wgrad_tma<NB><<<(unsigned)(cols * nsplit), WH_THREADS, S::SMEM, s>>>(act, dym, dw, N, D, H, W, Cin, Cout,
+                                                                                 nci, nco, (int)nsplit);
+    return cudaGetLastError();
+}
+
 cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
                          cudaStream_t s) {
+    // the brick form when the input channels come in blocks of 32 (or 16) and the output channels
+    // in groups of 8
+    if (Cout % 8 == 0 && encode_tiled()) {
+        if (Cin % 32 == 0) return launch_wgrad_tma<32>(in, dy, dw, N, D, H, W, Cin, Cout, s);
+        if (Cin % 16 == 0) return launch_wgrad_tma<16>(in, dy, dw, N, D, H, W, Cin, Cout, s);
+    }
     // channel blocks of CB <= 128 rows stacked with 128 / CB taps; other shapes on mma.sync
     const int CB = Cin <= 128 ? Cin : 64;
     if (Cin % 16 != 0 || Cout % 32 != 0 || Cin % CB != 0 || 128 % CB != 0 && Cin > 128)
