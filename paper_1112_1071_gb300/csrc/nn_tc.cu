@@ -734,23 +734,28 @@ constexpr int WH_HREG = (WH_HBYTES + 127) & ~127;         // its region, 128-byt
 constexpr int WH_DREG = BRICK_X * BRICK_Y * 16;           // one 8-channel dY brick: 2048 bytes
 constexpr int WH_DY = 16 * WH_DREG;                       // 128 output-channel rows: 32 KB
 
-template <int NB>
+// T = the transposed roles, for layers with more input than output channels: the halo view is A
+// (M = 128 input channels, zeroed rows past the real ones) and the dY brick B (N = NB output
+// channels); the accumulators then hold dW^T per tap.
+template <int NB, bool T>
 struct WhShape {
-    static constexpr int HALO = (NB / 8) * WH_HREG;
+    static constexpr int HREGS = T ? 16 : NB / 8;     // halo regions (8 input channels each)
+    static constexpr int DREGS = T ? NB / 8 : 16;     // dY regions (8 output channels each)
+    static constexpr int HALO = HREGS * WH_HREG;
     static constexpr int HALO_AL = (HALO + 1023) & ~1023;
-    static constexpr int STAGE = HALO_AL + WH_DY;
+    static constexpr int STAGE = HALO_AL + DREGS * WH_DREG;
     static constexpr int STAGES = 4;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 128;
     static constexpr uint32_t NCOLS = 9 * NB <= 256 ? 256 : 512;
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int NB>
+template <int NB, bool T>
 __global__ void __launch_bounds__(WH_THREADS, 1)
     k_conv3d_wgrad_tma(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap dym,
                        float* __restrict__ dw, int N, int D, int H, int W, int Cin, int Cout, int nci, int nco,
                        int nsplit) {
-    using S = WhShape<NB>;
+    using S = WhShape<NB, T>;
     constexpr int STAGE = S::STAGE, WS = S::STAGES;
     constexpr uint32_t NCOLS = S::NCOLS;
     // FP32 D, BF16 A and B, both MN-major (bits 15 and 16), M = 128, N = NB
@@ -776,8 +781,8 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
     c /= nco;
     const int cib = c % nci;
     const int dz = c / nci;
-    const int ci0 = cib * NB, co0 = cob * 128;
-    const int mreal = min(128, Cout - co0);           // output-channel rows that are real
+    const int ci0 = cib * (T ? 128 : NB), co0 = cob * (T ? NB : 128);
+    const int mreal = T ? min(128, Cin - ci0) : min(128, Cout - co0);   // M rows that are real
     const int nbx = (W + BRICK_X - 1) / BRICK_X, nby = (H + BRICK_Y - 1) / BRICK_Y;
     const long long nbricks = (long long)N * D * nby * nbx;
     const long long b0 = nbricks * split / nsplit, b1 = nbricks * (split + 1) / nsplit;
@@ -792,11 +797,12 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    // the dY regions of rows past mreal stay zero in every stage
+    // the M operand's regions of rows past mreal stay zero in every stage
     for (int st = 0; st < WS; ++st) {
-        const int zb = (mreal / 8) * WH_DREG;
-        uint4* z = reinterpret_cast<uint4*>(smem_raw + (base - raw) + st * STAGE + S::HALO_AL + zb);
-        for (int q = tid; q < (WH_DY - zb) / 16; q += WH_THREADS) z[q] = make_uint4(0u, 0u, 0u, 0u);
+        const int reg = T ? WH_HREG : WH_DREG;
+        const int from = (T ? 0 : S::HALO_AL) + (mreal / 8) * reg, to = (T ? 0 : S::HALO_AL) + 16 * reg;
+        uint4* z = reinterpret_cast<uint4*>(smem_raw + (base - raw) + st * STAGE + from);
+        for (int q = tid; q < (to - from) / 16; q += WH_THREADS) z[q] = make_uint4(0u, 0u, 0u, 0u);
     }
     tc::fence_proxy_async_smem();
     if (warp == 0) {
@@ -842,7 +848,8 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
         if (lane == 0) {
             tc::tma_prefetch_map(&act);
             tc::tma_prefetch_map(&dym);
-            const uint32_t tx = (uint32_t)((NB / 8) * WH_HBYTES + (mreal / 8) * WH_DREG);
+            const int hg = T ? mreal / 8 : NB / 8, dg = T ? NB / 8 : mreal / 8;   // boxes per stage
+            const uint32_t tx = (uint32_t)(hg * WH_HBYTES + dg * WH_DREG);
             long long it = 0;
             for (long long t = b0; t < b1; ++t, ++it) {
                 const int st = (int)(it % WS);
@@ -851,9 +858,9 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
                 decode(t, b, z, y0, x0);
                 const uint32_t sb = base + st * STAGE;
                 tc::mbar_arrive_expect_tx(full(st), tx);
-                for (int g = 0; g < NB / 8; ++g)
+                for (int g = 0; g < hg; ++g)
                     tc::tma_load_5d(sb + g * WH_HREG, &act, ci0 + 8 * g, x0 - 1, y0 - 1, z + dz - 1, b, full(st));
-                for (int g = 0; g < mreal / 8; ++g)
+                for (int g = 0; g < dg; ++g)
                     tc::tma_load_5d(sb + S::HALO_AL + g * WH_DREG, &dym, co0 + 8 * g, x0, y0, z, b, full(st));
             }
             // no copy may still be landing when the block leaves
@@ -873,19 +880,23 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
                 }
                 tc::fence_after_sync();
                 const uint32_t sb = base + st * STAGE;
-                // A: 8-voxel core matrices 128 B apart along K, 8-channel regions along M;
-                // B: the tap's view of the halo plane, 8-voxel rows 160 B apart along K
-                const uint64_t a0 = tc::smem_desc(sb + S::HALO_AL, 128, WH_DREG);
+                // dY brick: 8-voxel core matrices 128 B apart along K, 8-channel regions apart
+                // along M or N; halo: the tap's view of the plane, 8-voxel rows 160 B apart
+                const uint64_t d0 = tc::smem_desc(sb + S::HALO_AL, 128, WH_DREG);
                 const uint64_t h0 = tc::smem_desc(sb, WH_ROW, WH_HREG);
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
-                        const uint32_t aoff = (kk * 256) >> 4;
-                        const uint32_t boff = (((2 * kk + dy) * (BRICK_X + 2) + dx) * 16) >> 4;
-                        tc::mma_bf16(tmem + (uint32_t)(tap * NB), a0 + aoff, h0 + boff, IDESC,
-                                     (t > b0 || kk > 0) ? 1u : 0u);
+                        const uint32_t doff = (kk * 256) >> 4;
+                        const uint32_t hoff = (((2 * kk + dy) * (BRICK_X + 2) + dx) * 16) >> 4;
+                        if constexpr (T)
+                            tc::mma_bf16(tmem + (uint32_t)(tap * NB), h0 + hoff, d0 + doff, IDESC,
+                                         (t > b0 || kk > 0) ? 1u : 0u);
+                        else
+                            tc::mma_bf16(tmem + (uint32_t)(tap * NB), d0 + doff, h0 + hoff, IDESC,
+                                         (t > b0 || kk > 0) ? 1u : 0u);
                     }
                 }
                 tc::mma_commit(empty(st));
@@ -902,7 +913,7 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
         got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
         if (got && b1 > b0) {
             tc::fence_after_sync();
-            const int co = co0 + warp * 32 + lane;
+            const int m = warp * 32 + lane;               // this lane's M row
             const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
             for (int tap = 0; tap < 9; ++tap) {
@@ -911,10 +922,16 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
                 for (int c0 = 0; c0 < NB; c0 += 16) {
                     float v[16];
                     tc::tmem_ld16(row + (uint32_t)(tap * NB + c0), v);
-                    if (warp * 32 + lane < mreal) {
-                        float* dst = dw + ((long long)tp * Cin + ci0 + c0) * Cout + co;
+                    if (m < mreal) {
+                        if constexpr (T) {       // row = input channel, columns = output channels
+                            float* dst = dw + ((long long)tp * Cin + ci0 + m) * Cout + co0 + c0;
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) atomicAdd(dst + (long long)q * Cout, v[q]);
+                            for (int q = 0; q < 16; ++q) atomicAdd(dst + q, v[q]);
+                        } else {                 // row = output channel, columns = input channels
+                            float* dst = dw + ((long long)tp * Cin + ci0 + c0) * Cout + co0 + m;
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) atomicAdd(dst + (long long)q * Cout, v[q]);
+                        }
                     }
                 }
             }
@@ -925,10 +942,10 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
 }
 
-template <int NB>
+template <int NB, bool T>
 static cudaError_t launch_wgrad_tma(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin,
                                     int Cout, cudaStream_t s) {
-    using S = WhShape<NB>;
+    using S = WhShape<NB, T>;
     EncodeTiled enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap act, dym;
@@ -949,30 +966,33 @@ static cudaError_t launch_wgrad_tma(const bf16* in, const bf16* dy, float* dw, i
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_tma<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv3d_wgrad_tma<NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int nci = Cin / NB, nco = (Cout + 127) / 128;
+    const int nci = T ? (Cin + 127) / 128 : Cin / NB, nco = T ? Cout / NB : (Cout + 127) / 128;
     const long long nbricks = (long long)N * D * ((H + BRICK_Y - 1) / BRICK_Y) * ((W + BRICK_X - 1) / BRICK_X);
     const int cols = 3 * nci * nco;
     // one wave of one CTA per SM, at least 4 bricks per CTA
     long long nsplit = sms / cols;
     if (nsplit < 1) nsplit = 1;
     if (nsplit > nbricks / 4) nsplit = nbricks / 4 > 0 ? nbricks / 4 : 1;
-    k_conv3d_wgrad_tma<NB><<<(unsigned)(cols * nsplit), WH_THREADS, S::SMEM, s>>>(act, dym, dw, N, D, H, W, Cin, Cout,
-                                                                                 nci, nco, (int)nsplit);
+    k_conv3d_wgrad_tma<NB, T><<<(unsigned)(cols * nsplit), WH_THREADS, S::SMEM, s>>>(act, dym, dw, N, D, H, W, Cin,
+                                                                                    Cout, nci, nco, (int)nsplit);
     return cudaGetLastError();
 }
 
 cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
                          cudaStream_t s) {
-    // the brick form when the input channels come in blocks of 32 (or 16) and the output channels
-    // in groups of 8
-    if (Cout % 8 == 0 && encode_tiled()) {
-        if (Cin % 32 == 0) return launch_wgrad_tma<32>(in, dy, dw, N, D, H, W, Cin, Cout, s);
-        if (Cin % 16 == 0) return launch_wgrad_tma<16>(in, dy, dw, N, D, H, W, Cin, Cout, s);
+    // the brick form, its MMA rows (128) on the wider side: output channels (input channels in
+    // blocks of 32) or, with more input than output channels, input channels (output channels in
+    // blocks of 32); 16 input channels (the first layer) on the stacked-tap kernel below, which
+    // is faster there
+    if (encode_tiled() && Cin % 32 == 0 && Cout % 8 == 0) {
+        if (Cin > Cout && Cout % 32 == 0) return launch_wgrad_tma<32, true>(in, dy, dw, N, D, H, W, Cin, Cout, s);
+        return launch_wgrad_tma<32, false>(in, dy, dw, N, D, H, W, Cin, Cout, s);
     }
     // channel blocks of CB <= 128 rows stacked with 128 / CB taps; other shapes on mma.sync
     const int CB = Cin <= 128 ? Cin : 64;
