@@ -50,10 +50,12 @@ def test_conv3d_forward_matches_oracle(cin, cout, relu):
         close(got[s], ref, 8e-3)      # one BF16 rounding of the output
 
 
-@pytest.mark.parametrize("cin,cout", [(32, 64), (64, 128), (96, 32), (192, 64)])
+@pytest.mark.parametrize("cin,cout", [(32, 64), (64, 128), (96, 32), (192, 64), (32, 192)])
 def test_conv3d_backward_matches_oracle(cin, cout):
-    # weight gradients on tcgen05: 4, 2, 1 taps of all input channels and (192) 2 taps of 64-channel
-    # blocks stacked into the MMA's 128 rows
+    # weight gradients on tcgen05 in brick form: output channels in the MMA's rows (32 -> 64,
+    # 64 -> 128; 32 -> 192 in two blocks, the second with 64 real rows) or input channels (96 -> 32,
+    # 192 -> 64 in two blocks); the network's first layer (16 input channels) runs the stacked-tap
+    # kernel and is checked in the network gradient test
     torch = torch_cuda()
     rng = np.random.default_rng(7)
     n, d, h, w = 2, 4, 6, 8
