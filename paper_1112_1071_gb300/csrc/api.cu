@@ -49,13 +49,23 @@ struct DeviceGuard {
 };
 
 // ---------------------------------------------------------------- staging
+// rho L0 (density times the scaled unit of length), the walk's per-cell factor, formed in FP64
+// and rounded once
+__global__ void k_density_scaled(const float* __restrict__ rho, float* __restrict__ rhoL, int64_t n, double L0) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        rhoL[c] = (float)((double)rho[c] * L0);
+}
+
 int stage_grid(hrt_ctx* ctx) {
     const cudaStream_t s = ctx->stream;
     const int64_t nc = ctx->ncells();
-    std::vector<float> rhoL(nc);
-    for (int64_t c = 0; c < nc; ++c) rhoL[c] = (float)((double)ctx->rho[c] * ctx->L0);
-    CK(ctx->d_rhoL.upload(rhoL.data(), nc, s), "upload density");
     CK(ctx->d_rho.upload(ctx->rho.data(), nc, s), "upload density");
+    CK(ctx->d_rhoL.alloc(nc), "upload density");
+    {
+        const int64_t blocks = std::min<int64_t>((nc + 255) / 256, 65535 * 8);
+        k_density_scaled<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(ctx->d_rho.p, ctx->d_rhoL.p, nc, ctx->L0);
+        CK(cudaGetLastError(), "scale density");
+    }
     DevGrid& g = ctx->grid;
     g = DevGrid{};
     g.type = ctx->gtype;
