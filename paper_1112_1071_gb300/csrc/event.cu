@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256, MINB) k_event(DevGrid g, DevDust d, DevSo
     const SharedTallies st = shared_tallies(o, a);
     __shared__ unsigned long long cnt_sh[8][N_COUNTERS];
     LocalCounters lc;
-    lc.init(cnt_sh[threadIdx.x >> 5], !MRW);
+    lc.init(cnt_sh[threadIdx.x >> 5], MRW ? CNT_REG : CNT_GROUPED);
     const unsigned lane = threadIdx.x & 31u;
     auto fetch = [&](unsigned need, unsigned lt_mask) -> long long {
         unsigned long long base = 0;

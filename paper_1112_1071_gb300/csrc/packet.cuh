@@ -7,19 +7,32 @@
 
 namespace hrt {
 
-// Per-thread tallies of a propagation kernel.  The two per-crossing counts live in registers; the
-// per-event counts (escapes, interactions, ...: one per tens of crossings) go by shared-memory
-// atomics to the warp's slot, so a thread holds 4 registers of counters instead of 2 per counter.
-// `slot` is this warp's row of a kernel's __shared__ unsigned long long [8][N_COUNTERS] (blocks
-// of <= 256 threads).
+// Per-thread tallies of a propagation kernel.  The two per-crossing counts live in registers;
+// the per-event counts (escapes, interactions, ...: one per tens of crossings) go, in the default
+// mode, by shared-memory atomics to the warp's slot, so a thread holds 4 registers of counters
+// instead of 2 per counter.  `slot` is this warp's row of a kernel's __shared__ unsigned long long
+// [8][N_COUNTERS] (blocks of <= 256 threads).  Modes (a constant of each kernel):
+//   CNT_GROUPED: the lanes that reach one call site together add their count with one shared
+//     atomic (a thick model's events come in whole warps; 32 atomics on one address serialise);
+//   CNT_LANE: one shared atomic per lane;
+//   CNT_REG: every count in registers, as for the modified-random-walk kernels, whose steps are
+//     events and which run at 3 blocks per SM anyway (measured: grouped 45-49 % and per-lane
+//     atomics 2-15 % slower there).
+enum CounterMode : int { CNT_GROUPED = 0, CNT_LANE = 1, CNT_REG = 2 };
+
 struct LocalCounters {
     unsigned long long cross, peel_cross;
     unsigned long long* slot;
-    bool agg;                  // per-event counts added once per group of lanes (see inc)
-    __device__ __forceinline__ void init(unsigned long long* warp_slot, bool aggregate = true) {
+    int mode;
+    unsigned long long v[N_COUNTERS];      // CNT_REG
+    __device__ __forceinline__ void init(unsigned long long* warp_slot, int m = CNT_GROUPED) {
         cross = peel_cross = 0ull;
         slot = warp_slot;
-        agg = aggregate;
+        mode = m;
+        if (mode == CNT_REG) {
+#pragma unroll
+            for (int i = 0; i < N_COUNTERS; ++i) v[i] = 0ull;
+        }
         const unsigned lane = threadIdx.x & 31u;
         if (lane < (unsigned)N_COUNTERS) slot[lane] = 0ull;
         __syncwarp();
@@ -27,18 +40,17 @@ struct LocalCounters {
     __device__ __forceinline__ void add(int c, unsigned long long x) {
         if (c == C_CROSSINGS) cross += x;
         else if (c == C_PEEL_CROSSINGS) peel_cross += x;
+        else if (mode == CNT_REG) v[c] += x;
         else atomicAdd(slot + c, x);
     }
-    // With agg, the lanes that reach one call site together add their count with one shared
-    // atomic (a thick model's events come in whole warps; 32 atomics on one address serialise):
-    // measured 13-19 % faster on thick grey models, but 45-49 % slower in the modified-random-walk
-    // kernel, whose kernels therefore keep one atomic per lane.
     __device__ __forceinline__ void inc(int c) {
         if (c == C_CROSSINGS) {
             ++cross;
         } else if (c == C_PEEL_CROSSINGS) {
             ++peel_cross;
-        } else if (agg) {
+        } else if (mode == CNT_REG) {
+            ++v[c];
+        } else if (mode == CNT_GROUPED) {
             const unsigned m = __activemask();
             if ((threadIdx.x & 31u) == (unsigned)(__ffs(m) - 1)) atomicAdd(slot + c, (unsigned long long)__popc(m));
         } else {
@@ -59,6 +71,17 @@ __device__ __forceinline__ void flush_counters(LocalCounters& lc, unsigned long 
     }
     if (lane == 0 && x) atomicAdd(g + C_CROSSINGS, x);
     if (lane == 0 && y) atomicAdd(g + C_PEEL_CROSSINGS, y);
+    if (lc.mode == CNT_REG) {
+#pragma unroll
+        for (int i = 0; i < N_COUNTERS; ++i) {
+            if (i == C_CROSSINGS || i == C_PEEL_CROSSINGS) continue;
+            unsigned long long z = lc.v[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
+            if (lane == 0 && z) atomicAdd(g + i, z);
+            lc.v[i] = 0ull;
+        }
+    }
     __syncwarp();
     if (lane < (unsigned)N_COUNTERS && lane != (unsigned)C_CROSSINGS && lane != (unsigned)C_PEEL_CROSSINGS) {
         const unsigned long long z = lc.slot[lane];
