@@ -351,17 +351,16 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     const bool peel = job.args.peel != 0;
     // default shapes (measured on GB300): Lucy iterations at 4 blocks of 256 per SM (64
     // registers; with the L2 hints 5 % faster than 3 on the 256^3 cloud, 7 % on the disk despite
-    // some spilling there), 3 on cylindrical grids; imaging passes at 3 (80 registers: 6-8 %
-    // faster than 2 on the disk and the cloud).  Warps stay in the walk phase while at least 20
-    // lanes walk (Lucy), 16 (imaging: 7 % faster than 20 on the cloud), 24 on cylindrical grids
-    // (tuned at 3 blocks), 12 for Cartesian Lucy runs of < 4M packets, whose tail dominates
+    // some spilling there, 20 % on the cylindrical ISRF cloud, within 1 % on the cylindrical
+    // disk); imaging passes at 3 (80 registers: 6-8 % faster than 2 on the disk and the cloud).
+    // Warps stay in the walk phase while at least 20 lanes walk (Lucy), 16 (imaging: 7 % faster
+    // than 20 on the cloud), 12 for Cartesian Lucy runs of < 4M packets, whose tail dominates
     int rg_default = DEFAULT_REGROUP;
-    if (job.grid.type == GRID_CYLINDRICAL) rg_default = 24;
-    else if (peel) rg_default = 16;
-    else if (job.grid.type == GRID_SPHERICAL || job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
+    if (peel) rg_default = 16;
+    else if (job.grid.type != GRID_CARTESIAN || job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
-    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 3 : job.grid.type == GRID_CYLINDRICAL ? 3 : 4);
+    const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 3 : 4);
     cudaError_t e;
     if (job.grid.type == GRID_CARTESIAN)
         e = peel ? launch_event_shape<GRID_CARTESIAN, true>(j, ll, bps, s)
