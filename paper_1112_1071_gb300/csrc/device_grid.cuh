@@ -755,6 +755,19 @@ template <int G>
 __device__ __forceinline__ float tau_to_edge(const DevGrid& g, Ray r, float chi, unsigned long long& ncross,
                                              float tau_stop) {
     float tau = 0.f;
+    if constexpr (G == GRID_CARTESIAN) {
+        // the next wall of every axis in registers, one wall load per crossing (same arithmetic)
+        float3 wn = cart_next_walls(g, r);
+        for (unsigned steps = 0; steps < MAX_WALK_STEPS; ++steps) {
+            int axis;
+            const float l = cart_exit_w(r, wn, axis);
+            tau += __ldg(g.rhoL + r.ci) * chi * l;
+            ++ncross;
+            if (tau > tau_stop) return tau;
+            if (cart_step_w(g, r, wn, l, axis)) return tau;
+        }
+        return F_INF;
+    }
     int zero_run = 0;
     for (unsigned steps = 0; steps < MAX_WALK_STEPS; ++steps) {
         int axis, dir;
