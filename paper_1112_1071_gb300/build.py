@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     raise RuntimeError(f"nvcc failed on {j[-3]}")
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -11,6 +11,7 @@
 #include <limits>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hrt.h"
@@ -29,6 +30,44 @@ bool finite_all(const double* a, int64_t n) {
         if (!std::isfinite(a[i])) return false;
     return true;
 }
+// First index in [0, n) where ok(i) fails (n when none) and the number of i with count(i),
+// over up to 8 host threads for large arrays (the per-cell checks of a 256^3 grid take tens of
+// milliseconds on one core).
+template <class Ok, class Count>
+void scan_cells(int64_t n, Ok ok, Count count, int64_t& first_bad, int64_t& counted) {
+    const int64_t big = (int64_t)1 << 20;
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt < 1 ? 1 : (nt > 8 ? 8 : nt);
+    if (n < big || nt == 1) nt = 1;
+    std::vector<int64_t> bad(nt, n), cnt(nt, 0);
+    auto work = [&](unsigned w) {
+        const int64_t b = n * w / nt, e = n * (w + 1) / nt;
+        int64_t c = 0;
+        for (int64_t i = b; i < e; ++i) {
+            if (!ok(i)) {
+                bad[w] = i;
+                break;
+            }
+            c += count(i) ? 1 : 0;
+        }
+        cnt[w] = c;
+    };
+    if (nt == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned w = 1; w < nt; ++w) th.emplace_back(work, w);
+        work(0);
+        for (auto& t : th) t.join();
+    }
+    first_bad = n;
+    counted = 0;
+    for (unsigned w = 0; w < nt; ++w) {
+        first_bad = std::min(first_bad, bad[w]);
+        counted += cnt[w];
+    }
+}
+
 bool increasing(const double* a, int64_t n) {
     for (int64_t i = 1; i < n; ++i)
         if (!(a[i] > a[i - 1])) return false;
@@ -536,11 +575,10 @@ int hrt_set_density(hrt_ctx* ctx, const float* rho, int64_t n) {
     if (!ctx) return HRT_EINVAL;
     if (ctx->gtype < 0) return ctx->fail(HRT_ESTATE, "density before grid");
     if (!rho || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "density: expected %lld cells", (long long)ctx->ncells());
-    int64_t nd = 0;
-    for (int64_t c = 0; c < n; ++c) {
-        if (!std::isfinite(rho[c]) || rho[c] < 0.f) return ctx->fail(HRT_EINVAL, "density: cell %lld not finite and >= 0", (long long)c);
-        nd += rho[c] > 0.f;
-    }
+    int64_t nd = 0, bad = n;
+    scan_cells(n, [&](int64_t c) { return std::isfinite(rho[c]) && rho[c] >= 0.f; },
+               [&](int64_t c) { return rho[c] > 0.f; }, bad, nd);
+    if (bad < n) return ctx->fail(HRT_EINVAL, "density: cell %lld not finite and >= 0", (long long)bad);
     ctx->rho.assign(rho, rho + n);
     ctx->n_dust = nd;
     ctx->dirty_grid = true;
@@ -1163,8 +1201,12 @@ int hrt_set_temperature(hrt_ctx* ctx, const double* T, int64_t n) {
     if (!ctx) return HRT_EINVAL;
     if (ctx->gtype < 0 || (int64_t)ctx->rho.size() != ctx->ncells()) return ctx->fail(HRT_ESTATE, "set grid and density first");
     if (!T || n != ctx->ncells()) return ctx->fail(HRT_EINVAL, "temperature: expected %lld cells", (long long)ctx->ncells());
-    for (int64_t c = 0; c < n; ++c)
-        if (!(T[c] > 0) || !std::isfinite(T[c])) return ctx->fail(HRT_EINVAL, "temperature must be finite > 0");
+    {
+        int64_t bad = n, unused = 0;
+        scan_cells(n, [&](int64_t c) { return T[c] > 0 && std::isfinite(T[c]); }, [](int64_t) { return false; },
+                   bad, unused);
+        if (bad < n) return ctx->fail(HRT_EINVAL, "temperature must be finite > 0");
+    }
     DeviceGuard dg(ctx->device);
     if (ctx->dirty_grid) {
         int rc = stage_grid(ctx);
