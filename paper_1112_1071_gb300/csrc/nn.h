@@ -26,7 +26,7 @@ cudaError_t conv3d_mma(const bf16* in, const bf16* B, const float* bias, bf16* o
 cudaError_t tc_status(int* failed, cudaStream_t s);
 // dw [27][Cin][Cout] += sum over voxels (FP32 atomics; zero dw first).  conv3d_wgrad runs on the
 // tcgen05 tensor cores (nn_tc.cu): the brick form (halo loaded once for 9 taps by TMA) for
-// Cin % 16 == 0 and Cout % 8 == 0, else the stacked-tap form for Cin % 16 == 0 (<= 128, or a
+// Cin % 32 == 0 and Cout % 8 == 0, else the stacked-tap form for Cin % 16 == 0 (<= 128, or a
 // multiple of 64) and Cout % 32 == 0, other shapes on mma.sync (conv3d_wgrad_mma).
 cudaError_t conv3d_wgrad(const bf16* in, const bf16* dy, float* dw, int N, int D, int H, int W, int Cin, int Cout,
                          cudaStream_t s);
