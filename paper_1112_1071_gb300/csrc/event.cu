@@ -353,11 +353,14 @@ cudaError_t launch_propagate_event(const PropagateJob& job, const Launch& l, cud
     // registers; with the L2 hints 5 % faster than 3 on the 256^3 cloud, 7 % on the disk despite
     // some spilling there, 20 % on the cylindrical ISRF cloud, within 1 % on the cylindrical
     // disk); imaging passes at 3 (80 registers: 6-8 % faster than 2 on the disk and the cloud).
-    // Warps stay in the walk phase while at least 20 lanes walk (Lucy), 16 (imaging: 7 % faster
-    // than 20 on the cloud), 12 for Cartesian Lucy runs of < 4M packets, whose tail dominates
+    // Warps stay in the walk phase while at least 20 lanes walk (Lucy on curvilinear grids; 19
+    // on Cartesian runs of >= 4M packets: 1 % faster than 20 on the cloud), 16 (imaging: 7 %
+    // faster than 20 on the cloud), 12 for Cartesian Lucy runs of < 4M packets, whose tail
+    // dominates
     int rg_default = DEFAULT_REGROUP;
     if (peel) rg_default = 16;
-    else if (job.grid.type != GRID_CARTESIAN || job.args.n_packets >= (int64_t)1 << 22) rg_default = 20;
+    else if (job.grid.type != GRID_CARTESIAN) rg_default = 20;
+    else if (job.args.n_packets >= (int64_t)1 << 22) rg_default = 19;
     j.args.regroup = l.regroup > 0 ? (l.regroup > 32 ? 32 : l.regroup) : rg_default;
     *launched += 1;
     const int bps = l.blocks_per_sm > 0 ? l.blocks_per_sm : (peel ? 3 : 4);
